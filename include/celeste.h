@@ -1,0 +1,236 @@
+/*
+ * celeste.h -- C ABI of the GB300 (sm_103a) library for the per-source
+ * variational objective of Regier et al., "Approximate Inference for
+ * Constructing Astronomical Catalogs from Images" (arXiv:1803.00113).
+ *
+ * What the library computes, for each light source s of a request:
+ *   L_s(theta_s) = sum over the pixels m of s's patches in every image n of
+ *                  -E[lambda_nm] + x_nm (log E[lambda_nm]
+ *                                        - V[lambda_nm] / (2 E[lambda_nm]^2))
+ *                  - KL_s(theta_s),
+ * the delta-method ELBO of Eq. eq:log_p_last (Sec. 4.2.2) restricted to the
+ * terms that depend on theta_s, with E and V from Eqs. conditional and vareq
+ * and KL_s from Eq. kleq (Sec. 4.2.3, Supplement A); its exact gradient and
+ * dense Hessian over the 27 unconstrained coordinates of theta_s; and one
+ * Newton trust-region iteration on theta_s (Sec. 4.3).  -log x! is excluded.
+ *
+ * Conventions shared by every call
+ *  - All array pointers inside celeste_problem, and every output pointer,
+ *    are DEVICE pointers owned by the caller; the library never frees them.
+ *    Pointers named h_* are HOST pointers read during the call only.
+ *  - Every call is asynchronous on the context's stream.  The return value
+ *    reports argument validation and launch errors only (0 = OK, negative =
+ *    error, see CELESTE_E*); nothing aborts.  Device-side problems (a patch
+ *    outside its image, non-positive sky, a non-finite value) set bits in the
+ *    context's device error word, read and cleared by celeste_synchronize.
+ *  - Gradients and Hessians are of L_s itself (for maximisation).
+ *  - Units: pixel coordinates (x = column, y = row, pixel centres at
+ *    integers); reference-frame positions in pixels; fluxes in nanomaggies.
+ */
+#ifndef CELESTE_H
+#define CELESTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define CELESTE_OK            0
+#define CELESTE_EINVAL      (-1)   /* bad argument (null, size, range)      */
+#define CELESTE_ENOMEM      (-2)   /* device allocation failed              */
+#define CELESTE_ECUDA       (-3)   /* a CUDA call failed                    */
+#define CELESTE_EDEVICE     (-4)   /* device error word was nonzero         */
+#define CELESTE_EAGAIN      (-5)   /* serving: no capacity, retry later     */
+#define CELESTE_EBUSY       (-6)   /* serving: request not finished         */
+#define CELESTE_ENOTFOUND   (-7)   /* serving: unknown ticket               */
+
+/* device error word bits (celeste_synchronize returns CELESTE_EDEVICE and
+ * stores the word in *device_error when any is set) */
+#define CELESTE_DERR_PATCH     0x1u  /* patch rectangle outside its image */
+#define CELESTE_DERR_SKY       0x2u  /* sky <= 0 at a patch pixel          */
+#define CELESTE_DERR_NONFINITE 0x4u  /* non-finite value/gradient/Hessian */
+#define CELESTE_DERR_TIMEOUT   0x8u  /* a bounded device wait gave up      */
+
+/* ---- sizes ------------------------------------------------------------ */
+#define CELESTE_N_THETA      27   /* Newton block per source (see layout)  */
+#define CELESTE_N_BANDS       5   /* u, g, r, i, z (Table 1: B = 5)        */
+#define CELESTE_N_PSF         3   /* Gaussian components of each PSF       */
+#define CELESTE_MAX_PROFILE   8   /* components per galaxy profile (K)     */
+#define CELESTE_MAX_COLOR     8   /* colour prior components per type (J)  */
+
+/* ---- layout of theta (27 unconstrained doubles per source) -------------
+ * Type 0 = galaxy, 1 = star; q(a_s = 1) is the star probability (Eq. eq0).
+ *   0        logit q(a = star)
+ *   1, 2     galaxy: mean of log r, log variance of log r   (q(r | a=0))
+ *   3, 4     star:   mean of log r, log variance of log r   (q(r | a=1))
+ *   5..8     galaxy colour means     9..12  star colour means
+ *   13..16   galaxy log colour variances   17..20 star log colour variances
+ *   21, 22   position u (x, y) in the reference frame (point mass)
+ *   23       major-axis angle, radians; 24 log half-light radius (pixels);
+ *   25       logit minor/major axis ratio; 26 logit profile weight (the
+ *            weight of the exponential profile; de Vaucouleurs gets 1 - it)
+ * Reference band r = band index 2; colour c_k = log(l_{k+1} / l_k).
+ */
+
+/* Model constants (host struct, copied into the context at creation).
+ * Galaxy profiles: Eq. eq:hsi, component j of profile p has weight
+ * alpha_p[j] and covariance tau_p[j] * Sigma_s.  Priors: Sec. 2.1 and
+ * Table 3 (prior_r: mean and variance of log r per type; colour prior: a
+ * J-component Gaussian mixture per type; e_radius: mean and variance of log
+ * radius; e_profile, e_axis: Beta parameters). */
+typedef struct celeste_model {
+  int32_t n_exp, n_dev, n_color, reserved;
+  double alpha_exp[CELESTE_MAX_PROFILE], tau_exp[CELESTE_MAX_PROFILE];
+  double alpha_dev[CELESTE_MAX_PROFILE], tau_dev[CELESTE_MAX_PROFILE];
+  double prior_a;
+  double prior_r[2][2];
+  double color_w[2][CELESTE_MAX_COLOR];
+  double color_mean[2][CELESTE_MAX_COLOR][4];
+  double color_cov[2][CELESTE_MAX_COLOR][4][4];
+  double e_radius[2], e_profile[2], e_axis[2];
+} celeste_model;
+
+/* One image (Sec. 2.2), 256 bytes, element of a DEVICE array.
+ * pixels[pix_offset + row * row_stride + col] is the photon count x_nm.
+ * Sky: sky_ny x sky_nx knots at sky[sky_offset + i * sky_nx + j], spanning
+ * the image (knot (i, j) at x = j (width-1)/(sky_nx-1), y = i (height-1)/
+ * (sky_ny-1)), interpolated bilinearly; must be > 0.  calib: photons per
+ * nanomaggy.  WCS: pixel position = wcs_A (row-major 2x2) * u + wcs_t.
+ * psf[k] = {weight, mean x, mean y, cov xx, cov xy, cov yy}. */
+typedef struct celeste_image {
+  int64_t pix_offset, sky_offset;
+  int32_t band, height, width, row_stride;
+  int32_t sky_ny, sky_nx, reserved0, reserved1;
+  double calib;
+  double wcs_A[4];
+  double wcs_t[2];
+  double psf[CELESTE_N_PSF][6];
+  double reserved2;
+} celeste_image;
+
+/* One patch: the pixels [x0, x0+w) x [y0, y0+h) of an image that source s
+ * lights (the support restriction of Sec. 2.2.3); 32 bytes.  A patch must
+ * lie inside its image.  pool_offset: where the patch's w*h pixels (row
+ * major) start in the patch-pixel pool used by celeste_render/background. */
+typedef struct celeste_patch {
+  int32_t image, x0, y0, w, h, reserved;
+  int64_t pool_offset;
+} celeste_patch;
+
+/* A problem: images, sources, patches, neighbours.  Device arrays unless
+ * named h_*.  Source s owns patches[patch_ptr[s] .. patch_ptr[s+1]) and its
+ * neighbours (sources whose patches overlap s's) are nbr_idx[nbr_ptr[s] ..
+ * nbr_ptr[s+1]).  The h_* copies of the index arrays are read by
+ * celeste_plan_create only. */
+typedef struct celeste_problem {
+  const float* pixels;
+  const float* sky;
+  const celeste_image* images;
+  double* theta;                  /* [n_sources][27]; newton_step updates it */
+  const int32_t* patch_ptr;
+  const celeste_patch* patches;
+  const int32_t* nbr_ptr;
+  const int32_t* nbr_idx;
+  const int32_t* h_patch_ptr;
+  const celeste_patch* h_patches;
+  const celeste_image* h_images;
+  const int32_t* h_nbr_ptr;
+  const int32_t* h_nbr_idx;
+  int64_t n_pixels, n_sky, n_pool;
+  int32_t n_images, n_sources, n_patches, n_nbr;
+} celeste_problem;
+
+/* Tile shape of the pixel kernels (picked per patch-size bucket by the
+ * autotuner in the Python layer; zeros select the defaults). */
+typedef struct celeste_tuning {
+  int32_t pixels_per_item;    /* pixels one warp reduces at a time (32..4096) */
+  int32_t warps_per_block;    /* 1..16 */
+  int32_t blocks_per_sm;      /* persistent grid = SMs * blocks_per_sm (0 = max resident) */
+  int32_t reserved;
+} celeste_tuning;
+
+typedef struct celeste_ctx celeste_ctx;
+typedef struct celeste_plan celeste_plan;
+
+/* Creates a context on `device` that launches on `cuda_stream` (a
+ * cudaStream_t, or NULL for the legacy default stream).  Copies *model.
+ * Returns CELESTE_EINVAL for out-of-range model sizes. */
+int celeste_create(celeste_ctx** out, const celeste_model* model, int device, void* cuda_stream);
+int celeste_destroy(celeste_ctx* ctx);
+/* Waits for the context's stream; returns CELESTE_EDEVICE (and the word in
+ * *device_error, may be NULL) if a device error bit was set, then clears it. */
+int celeste_synchronize(celeste_ctx* ctx, uint32_t* device_error);
+/* Number of kernel launches this context has issued (for accounting). */
+int64_t celeste_launch_count(const celeste_ctx* ctx);
+
+/* A plan binds a list of sources of a problem to a work decomposition
+ * (per source, image and pixel tile) and owns the device scratch of the
+ * calls below (component tables, background buffers, per-tile partial
+ * sums, Newton state).  h_src_ids: HOST array of n distinct source ids.
+ * Sources of one plan are updated together by celeste_newton_step, so they
+ * should not overlap (one colour class of the overlap graph, Sec. 4.4).
+ * tuning may be NULL.  The plan keeps pointers into *problem's arrays, not
+ * the struct itself; it stays valid while those arrays do. */
+int celeste_plan_create(celeste_ctx* ctx, const celeste_problem* problem,
+                        const int32_t* h_src_ids, int32_t n, const celeste_tuning* tuning,
+                        celeste_plan** out);
+int celeste_plan_destroy(celeste_plan* plan);
+/* Visits (source-pixel pairs) of one evaluation of the plan. */
+int64_t celeste_plan_visits(const celeste_plan* plan);
+
+/* L_s, its gradient and Hessian for every source of the plan (Eqs. elbo,
+ * eq:log_p_last, conditional, vareq, kleq).  Outputs (device, n = plan
+ * size, in plan order): elbo[n] = L_s; elbo_rel[n] = L_s minus the value
+ * with source s absent (sky and neighbours only), may be NULL; grad[n][27];
+ * hess[n][27][27] (full, symmetric).  Neighbours are frozen at theta. */
+int celeste_elbo_grad_hess(celeste_ctx* ctx, const celeste_plan* plan,
+                           double* elbo, double* elbo_rel, double* grad, double* hess);
+
+/* Value only (no derivatives): elbo[n] and elbo_rel[n] (either may be NULL). */
+int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, double* elbo_rel);
+
+/* One trust-region Newton iteration (Sec. 4.3) on every source of the plan
+ * whose status is not CONVERGED/FAILED: evaluate L_s, g, H at theta; solve
+ * max g.p + p.H.p/2 s.t. |p| <= delta exactly in FP64; evaluate L_s at
+ * theta + p; accept when the ratio of actual to predicted gain exceeds 0.1;
+ * update the radius (shrink to |p|/4 below 1/4, double up to 100 above 3/4
+ * when the step reached the boundary).  delta[n_sources] and
+ * status[n_sources] (device, indexed by source id) carry the state between
+ * calls; initialise delta to 1 and status to 0.  Status values:
+ * CELESTE_ST_*.  elbo_rel (device [n], plan order, may be NULL) receives
+ * L_s - L_s(absent) at the iterate before the step. */
+#define CELESTE_ST_ACCEPTED   0
+#define CELESTE_ST_REJECTED   1
+#define CELESTE_ST_CONVERGED  2
+#define CELESTE_ST_MAXITER    3
+#define CELESTE_ST_FAILED    (-1)
+int celeste_newton_step(celeste_ctx* ctx, const celeste_plan* plan,
+                        double* delta, int32_t* status, double* elbo_rel);
+
+/* Only the FP64 trust-region subproblem, for n independent problems:
+ * maximise g.p + p.H.p/2 subject to |p| <= delta (Sec. 4.3).  g[n][27],
+ * H[n][27][27], delta[n] in; p[n][27], pred[n] (= g.p + p.H.p/2) out; all
+ * device arrays. */
+int celeste_tr_subproblem(celeste_ctx* ctx, int32_t n, const double* g, const double* H,
+                          const double* delta, double* p, double* pred);
+
+/* Rendering (Sec. 2.2.3, Eqs. conditional and vareq): for every patch of
+ * every plan source, the source's own E_q[l f] and V_q[l f] at each patch
+ * pixel, written to E_out/V_out at the patch's pool_offset (row major). */
+int celeste_render(celeste_ctx* ctx, const celeste_plan* plan, float* E_out, float* V_out);
+/* Sky plus the moments of the neighbours at each patch pixel of every
+ * plan source (the background a source is fitted against). */
+int celeste_background(celeste_ctx* ctx, const celeste_plan* plan, float* bgE_out, float* bgV_out);
+
+/* Greedy colouring of the overlap graph by ascending source id (host):
+ * colour[s] = smallest colour unused by lower-id neighbours.  Returns the
+ * number of colours, or a negative error. */
+int celeste_color_sources(int32_t n_sources, const int32_t* h_nbr_ptr, const int32_t* h_nbr_idx,
+                          int32_t* h_color_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CELESTE_H */

@@ -1,0 +1,362 @@
+"""Python binding of the CUDA library (``include/celeste.h``) via ctypes.
+
+Argument marshalling only: every step of the objective, its derivatives and
+the Newton step runs in the library's kernels.  PyTorch provides device
+memory and the stream.  The binding refuses to run without the compiled
+library and a CUDA device; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build_lib
+
+N_THETA = 27
+ST_ACCEPTED, ST_REJECTED, ST_CONVERGED, ST_MAXITER, ST_FAILED = 0, 1, 2, 3, -1
+
+IMAGE_DTYPE = np.dtype([
+    ("pix_offset", "<i8"), ("sky_offset", "<i8"),
+    ("band", "<i4"), ("height", "<i4"), ("width", "<i4"), ("row_stride", "<i4"),
+    ("sky_ny", "<i4"), ("sky_nx", "<i4"), ("reserved0", "<i4"), ("reserved1", "<i4"),
+    ("calib", "<f8"), ("wcs_A", "<f8", (4,)), ("wcs_t", "<f8", (2,)),
+    ("psf", "<f8", (3, 6)), ("reserved2", "<f8")])
+PATCH_DTYPE = np.dtype([("image", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("w", "<i4"),
+                        ("h", "<i4"), ("reserved", "<i4"), ("pool_offset", "<i8")])
+assert IMAGE_DTYPE.itemsize == 256 and PATCH_DTYPE.itemsize == 32
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("n_exp", ctypes.c_int32), ("n_dev", ctypes.c_int32),
+                ("n_color", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("alpha_exp", ctypes.c_double * 8), ("tau_exp", ctypes.c_double * 8),
+                ("alpha_dev", ctypes.c_double * 8), ("tau_dev", ctypes.c_double * 8),
+                ("prior_a", ctypes.c_double), ("prior_r", ctypes.c_double * 4),
+                ("color_w", ctypes.c_double * 16), ("color_mean", ctypes.c_double * 64),
+                ("color_cov", ctypes.c_double * 256), ("e_radius", ctypes.c_double * 2),
+                ("e_profile", ctypes.c_double * 2), ("e_axis", ctypes.c_double * 2)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "pixels", "sky", "images", "theta", "patch_ptr", "patches", "nbr_ptr", "nbr_idx",
+        "h_patch_ptr", "h_patches", "h_images", "h_nbr_ptr", "h_nbr_idx")] + [
+        ("n_pixels", ctypes.c_int64), ("n_sky", ctypes.c_int64), ("n_pool", ctypes.c_int64),
+        ("n_images", ctypes.c_int32), ("n_sources", ctypes.c_int32),
+        ("n_patches", ctypes.c_int32), ("n_nbr", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("pixels_per_item", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded library; raises if it was not built or CUDA is unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(build_lib.LIB):
+        raise RuntimeError(f"{build_lib.LIB} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(build_lib.LIB)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "celeste_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(_Model), ctypes.c_int, P]),
+        "celeste_destroy": (ctypes.c_int, [P]),
+        "celeste_synchronize": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32)]),
+        "celeste_launch_count": (I64, [P]),
+        "celeste_plan_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem), P, I32,
+                                               ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
+        "celeste_plan_destroy": (ctypes.c_int, [P]),
+        "celeste_plan_visits": (I64, [P]),
+        "celeste_elbo_grad_hess": (ctypes.c_int, [P, P, P, P, P, P]),
+        "celeste_elbo": (ctypes.c_int, [P, P, P, P]),
+        "celeste_newton_step": (ctypes.c_int, [P, P, P, P, P]),
+        "celeste_tr_subproblem": (ctypes.c_int, [P, I32, P, P, P, P, P]),
+        "celeste_render": (ctypes.c_int, [P, P, P, P]),
+        "celeste_background": (ctypes.c_int, [P, P, P, P]),
+        "celeste_color_sources": (ctypes.c_int, [I32, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def exported_symbols():
+    """Names the header declares, for the load check."""
+    return ["celeste_create", "celeste_destroy", "celeste_synchronize", "celeste_launch_count",
+            "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
+            "celeste_elbo_grad_hess", "celeste_elbo", "celeste_newton_step",
+            "celeste_tr_subproblem", "celeste_render", "celeste_background",
+            "celeste_color_sources"]
+
+
+class CelesteError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise CelesteError(f"{what} failed with code {rc}")
+    return rc
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def model_struct(model) -> _Model:
+    m = _Model()
+    m.n_exp, m.n_dev = len(model.alpha_exp), len(model.alpha_dev)
+    m.n_color = model.color_w.shape[1]
+    for name in ("alpha_exp", "tau_exp", "alpha_dev", "tau_dev"):
+        arr = getattr(m, name)
+        for j, x in enumerate(getattr(model, name)):
+            arr[j] = float(x)
+    m.prior_a = float(model.prior_a)
+    for k, x in enumerate(np.asarray(model.prior_r, dtype=np.float64).ravel()):
+        m.prior_r[k] = x
+    J = m.n_color
+    w = np.zeros((2, 8)); w[:, :J] = model.color_w
+    mu = np.zeros((2, 8, 4)); mu[:, :J] = model.color_mean
+    cov = np.tile(np.eye(4), (2, 8, 1, 1)); cov[:, :J] = model.color_cov
+    for k, x in enumerate(w.ravel()):
+        m.color_w[k] = x
+    for k, x in enumerate(mu.ravel()):
+        m.color_mean[k] = x
+    for k, x in enumerate(cov.ravel()):
+        m.color_cov[k] = x
+    for name in ("e_radius", "e_profile", "e_axis"):
+        arr = getattr(m, name)
+        for k, x in enumerate(getattr(model, name)):
+            arr[k] = float(x)
+    return m
+
+
+class Context:
+    """A library context bound to a device and to torch's current stream."""
+
+    def __init__(self, model, device: int = 0):
+        if not torch.cuda.is_available():
+            raise CelesteError("no CUDA device: the library has no CPU path")
+        self.device = torch.device("cuda", device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self._model = model_struct(model)
+        h = ctypes.c_void_p()
+        _check(lib().celeste_create(ctypes.byref(h), ctypes.byref(self._model), device,
+                                    ctypes.c_void_p(self.stream.cuda_stream)), "celeste_create")
+        self.handle = h
+
+    def synchronize(self):
+        w = ctypes.c_uint32(0)
+        rc = lib().celeste_synchronize(self.handle, ctypes.byref(w))
+        if rc < 0:
+            raise CelesteError(f"device error word 0x{w.value:x} (code {rc})")
+
+    def launches(self) -> int:
+        return int(lib().celeste_launch_count(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceProblem:
+    """A fields.Problem uploaded to the device (plus the host index copies)."""
+
+    def __init__(self, problem, device=None):
+        dev = device or torch.device("cuda", 0)
+        self.host = problem
+        p = problem
+        img = np.zeros(p.n_images, dtype=IMAGE_DTYPE)
+        img["pix_offset"] = p.img_pix_off
+        img["sky_offset"] = p.img_sky_off
+        img["band"] = p.img_band
+        img["height"] = p.img_h
+        img["width"] = p.img_w
+        img["row_stride"] = p.img_stride
+        img["sky_ny"] = p.img_sky_ny
+        img["sky_nx"] = p.img_sky_nx
+        img["calib"] = p.img_calib
+        img["wcs_A"] = p.img_A.reshape(-1, 4)
+        img["wcs_t"] = p.img_t
+        img["psf"] = p.img_psf
+        pat = np.zeros(p.n_patches, dtype=PATCH_DTYPE)
+        pat["image"] = p.patch_img
+        pat["x0"] = p.patch_x0
+        pat["y0"] = p.patch_y0
+        pat["w"] = p.patch_w
+        pat["h"] = p.patch_h
+        area = p.patch_w.astype(np.int64) * p.patch_h.astype(np.int64)
+        pat["pool_offset"] = np.concatenate([[0], np.cumsum(area)[:-1]]) if len(area) else []
+        self.n_pool = int(area.sum())
+        self.pool_offset = pat["pool_offset"].copy()
+        self.h_images = img
+        self.h_patches = pat
+        self.h_patch_ptr = np.ascontiguousarray(p.patch_ptr, dtype=np.int32)
+        self.h_nbr_ptr = np.ascontiguousarray(p.nbr_ptr, dtype=np.int32)
+        self.h_nbr_idx = np.ascontiguousarray(p.nbr_idx, dtype=np.int32)
+        if self.h_nbr_idx.size == 0:
+            self.h_nbr_idx = np.zeros(1, dtype=np.int32)
+
+        def up(a, dtype=None):
+            t = torch.from_numpy(np.ascontiguousarray(a if dtype is None else a.astype(dtype)))
+            return t.to(dev)
+
+        self.pixels = up(p.pixels, np.float32)
+        self.sky = up(p.sky, np.float32)
+        self.images = up(img.view(np.uint8))
+        self.theta = up(p.theta, np.float64)
+        self.patch_ptr = up(self.h_patch_ptr)
+        self.patches = up(pat.view(np.uint8))
+        self.nbr_ptr = up(self.h_nbr_ptr)
+        self.nbr_idx = up(self.h_nbr_idx)
+        s = _Problem()
+        s.pixels, s.sky, s.images = self.pixels.data_ptr(), self.sky.data_ptr(), self.images.data_ptr()
+        s.theta = self.theta.data_ptr()
+        s.patch_ptr, s.patches = self.patch_ptr.data_ptr(), self.patches.data_ptr()
+        s.nbr_ptr, s.nbr_idx = self.nbr_ptr.data_ptr(), self.nbr_idx.data_ptr()
+        s.h_patch_ptr = self.h_patch_ptr.ctypes.data
+        s.h_patches = self.h_patches.ctypes.data
+        s.h_images = self.h_images.ctypes.data
+        s.h_nbr_ptr = self.h_nbr_ptr.ctypes.data
+        s.h_nbr_idx = self.h_nbr_idx.ctypes.data
+        s.n_pixels, s.n_sky, s.n_pool = p.pixels.size, p.sky.size, self.n_pool
+        s.n_images, s.n_sources, s.n_patches = p.n_images, p.n_sources, p.n_patches
+        s.n_nbr = int(p.nbr_idx.size)
+        self.struct = s
+
+    @property
+    def n_sources(self):
+        return self.host.n_sources
+
+    def set_theta(self, theta):
+        self.theta.copy_(torch.as_tensor(np.asarray(theta, dtype=np.float64)).to(self.theta.device))
+
+
+class Plan:
+    """Work decomposition and scratch for a list of sources of a problem."""
+
+    def __init__(self, ctx: Context, dprob: DeviceProblem, sources: Sequence[int],
+                 pixels_per_item: int = 0, blocks_per_sm: int = 0):
+        self.ctx = ctx
+        self.dprob = dprob
+        self.sources = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        self.n = int(self.sources.size)
+        t = _Tuning(pixels_per_item, 0, blocks_per_sm, 0)
+        h = ctypes.c_void_p()
+        _check(lib().celeste_plan_create(ctx.handle, ctypes.byref(dprob.struct),
+                                         self.sources.ctypes.data if self.n else None, self.n,
+                                         ctypes.byref(t), ctypes.byref(h)), "celeste_plan_create")
+        self.handle = h
+        self.visits = int(lib().celeste_plan_visits(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def elbo_grad_hess(plan: Plan, out=None):
+    """(elbo, elbo_rel, grad [n, 27], hess [n, 27, 27]) as float64 device tensors."""
+    dev = plan.ctx.device
+    n = plan.n
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, device=dev),
+               torch.empty(n, dtype=torch.float64, device=dev),
+               torch.empty(n, N_THETA, dtype=torch.float64, device=dev),
+               torch.empty(n, N_THETA, N_THETA, dtype=torch.float64, device=dev))
+    e, er, g, H = out
+    _check(lib().celeste_elbo_grad_hess(plan.ctx.handle, plan.handle, _ptr(e), _ptr(er), _ptr(g),
+                                        _ptr(H)), "celeste_elbo_grad_hess")
+    return out
+
+
+def elbo(plan: Plan):
+    dev = plan.ctx.device
+    e = torch.empty(plan.n, dtype=torch.float64, device=dev)
+    er = torch.empty(plan.n, dtype=torch.float64, device=dev)
+    _check(lib().celeste_elbo(plan.ctx.handle, plan.handle, _ptr(e), _ptr(er)), "celeste_elbo")
+    return e, er
+
+
+def newton_step(plan: Plan, delta: torch.Tensor, status: torch.Tensor,
+                elbo_rel: Optional[torch.Tensor] = None):
+    """One trust-region iteration; delta/status are [n_sources] device tensors."""
+    _check(lib().celeste_newton_step(plan.ctx.handle, plan.handle, _ptr(delta), _ptr(status),
+                                     _ptr(elbo_rel)), "celeste_newton_step")
+
+
+def newton_state(dprob: DeviceProblem):
+    dev = dprob.theta.device
+    return (torch.ones(dprob.n_sources, dtype=torch.float64, device=dev),
+            torch.zeros(dprob.n_sources, dtype=torch.int32, device=dev))
+
+
+def tr_subproblem(ctx: Context, g: torch.Tensor, H: torch.Tensor, delta: torch.Tensor):
+    n = g.shape[0]
+    g = g.contiguous().to(torch.float64)
+    H = H.contiguous().to(torch.float64)
+    delta = delta.contiguous().to(torch.float64)
+    p = torch.empty_like(g)
+    pred = torch.empty(n, dtype=torch.float64, device=g.device)
+    _check(lib().celeste_tr_subproblem(ctx.handle, n, _ptr(g), _ptr(H), _ptr(delta), _ptr(p),
+                                       _ptr(pred)), "celeste_tr_subproblem")
+    return p, pred
+
+
+def render(plan: Plan):
+    """Own E and V of every plan source, in the problem's patch-pool layout."""
+    dev = plan.ctx.device
+    E = torch.zeros(plan.dprob.n_pool, dtype=torch.float32, device=dev)
+    V = torch.zeros(plan.dprob.n_pool, dtype=torch.float32, device=dev)
+    _check(lib().celeste_render(plan.ctx.handle, plan.handle, _ptr(E), _ptr(V)), "celeste_render")
+    return E, V
+
+
+def background(plan: Plan):
+    dev = plan.ctx.device
+    E = torch.zeros(plan.dprob.n_pool, dtype=torch.float32, device=dev)
+    V = torch.zeros(plan.dprob.n_pool, dtype=torch.float32, device=dev)
+    _check(lib().celeste_background(plan.ctx.handle, plan.handle, _ptr(E), _ptr(V)),
+           "celeste_background")
+    return E, V
+
+
+def color_sources(nbr_ptr: np.ndarray, nbr_idx: np.ndarray) -> np.ndarray:
+    """Greedy colouring of the overlap graph by ascending source id."""
+    n = len(nbr_ptr) - 1
+    ptr = np.ascontiguousarray(nbr_ptr, dtype=np.int32)
+    idx = np.ascontiguousarray(nbr_idx if len(nbr_idx) else np.zeros(1), dtype=np.int32)
+    col = np.zeros(max(n, 1), dtype=np.int32)
+    rc = lib().celeste_color_sources(n, ptr.ctypes.data, idx.ctypes.data, col.ctypes.data)
+    _check(rc, "celeste_color_sources")
+    return col[:n]
+
+
+def color_classes(problem) -> list:
+    col = color_sources(problem.nbr_ptr, problem.nbr_idx)
+    return [np.flatnonzero(col == c).astype(np.int32) for c in range(int(col.max()) + 1 if len(col) else 0)]

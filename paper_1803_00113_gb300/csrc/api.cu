@@ -1,0 +1,485 @@
+// C ABI of the library: contexts, plans (work decomposition and scratch),
+// and the calls of celeste.h, each a short sequence of kernel launches on the
+// context's stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace celeste;
+
+struct celeste_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  ModelDev* d_model = nullptr;
+  unsigned int* d_err = nullptr;
+  int n_exp = 0, n_dev = 0;
+  int64_t launches = 0;
+};
+
+struct celeste_plan {
+  celeste_ctx* ctx = nullptr;
+  PlanView v{};
+  const celeste_patch* d_patches = nullptr;
+  double* rel_trial = nullptr;
+  std::vector<void*> allocs;
+  int64_t visits = 0;
+  celeste_tuning tuning{};
+};
+
+namespace {
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return CELESTE_ECUDA; \
+  } while (0)
+
+int to_status(cudaError_t e) { return e == cudaSuccess ? CELESTE_OK : CELESTE_ECUDA; }
+
+Launch make_launch(const celeste_ctx* c, const celeste_plan* p) {
+  Launch L;
+  L.stream = c->stream;
+  L.sm_count = c->sm_count;
+  L.warps_per_block = p && p->tuning.warps_per_block > 0 ? p->tuning.warps_per_block : 4;
+  L.blocks_per_sm = p && p->tuning.blocks_per_sm > 0 ? p->tuning.blocks_per_sm : 3;
+  L.pixels_per_item = p && p->tuning.pixels_per_item > 0 ? p->tuning.pixels_per_item : 256;
+  L.n_exp = c->n_exp;
+  L.n_dev = c->n_dev;
+  return L;
+}
+
+// Inverse and log-determinant of a symmetric positive-definite 4x4 matrix
+// (Cholesky).  Returns false when it is not positive definite.
+bool spd_inverse4(const double C[4][4], double P[4][4], double* logdet) {
+  double L[4][4] = {{0}};
+  double ld = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = C[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[i][i] = sqrt(s);
+        ld += 2.0 * log(L[i][i]);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  }
+  // inverse of L, then P = L^-T L^-1
+  double Li[4][4] = {{0}};
+  for (int i = 0; i < 4; ++i) {
+    Li[i][i] = 1.0 / L[i][i];
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s -= L[i][k] * Li[k][j];
+      Li[i][j] = s / L[i][i];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = std::max(i, j); k < 4; ++k) s += Li[k][i] * Li[k][j];
+      P[i][j] = s;
+    }
+  *logdet = ld;
+  return true;
+}
+
+template <typename T>
+T* dev_alloc(celeste_plan* p, size_t count, int* err) {
+  if (count == 0) count = 1;
+  void* ptr = nullptr;
+  if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) {
+    *err = CELESTE_ENOMEM;
+    return nullptr;
+  }
+  p->allocs.push_back(ptr);
+  return static_cast<T*>(ptr);
+}
+
+int run_setup(celeste_ctx* c, celeste_plan* p, int first, int n, bool trial) {
+  Launch L = make_launch(c, p);
+  ++c->launches;
+  return to_status(launch_setup(L, p->v, c->d_model, first, n, trial));
+}
+
+}  // namespace
+
+extern "C" {
+
+int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* stream) {
+  if (!out || !m) return CELESTE_EINVAL;
+  *out = nullptr;
+  if (m->n_exp < 1 || m->n_exp > kMaxProf || m->n_dev < 1 || m->n_dev > kMaxProf ||
+      m->n_color < 1 || m->n_color > kMaxColor)
+    return CELESTE_EINVAL;
+  if (!(m->prior_a > 0.0 && m->prior_a < 1.0)) return CELESTE_EINVAL;
+  ModelDev md;
+  memset(&md, 0, sizeof(md));
+  md.n_exp = m->n_exp;
+  md.n_dev = m->n_dev;
+  md.n_color = m->n_color;
+  for (int j = 0; j < kMaxProf; ++j) {
+    md.alpha_exp[j] = m->alpha_exp[j];
+    md.tau_exp[j] = m->tau_exp[j];
+    md.alpha_dev[j] = m->alpha_dev[j];
+    md.tau_dev[j] = m->tau_dev[j];
+  }
+  md.prior_a = m->prior_a;
+  for (int i = 0; i < 2; ++i) {
+    if (!(m->prior_r[i][1] > 0.0)) return CELESTE_EINVAL;
+    md.prior_r[i][0] = m->prior_r[i][0];
+    md.prior_r[i][1] = m->prior_r[i][1];
+    for (int j = 0; j < m->n_color; ++j) {
+      if (!(m->color_w[i][j] > 0.0)) return CELESTE_EINVAL;
+      md.color_w[i][j] = m->color_w[i][j];
+      for (int k = 0; k < 4; ++k) md.color_mean[i][j][k] = m->color_mean[i][j][k];
+      if (!spd_inverse4(m->color_cov[i][j], md.color_prec[i][j], &md.color_logdet[i][j]))
+        return CELESTE_EINVAL;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    md.e_radius[k] = m->e_radius[k];
+    md.e_profile[k] = m->e_profile[k];
+    md.e_axis[k] = m->e_axis[k];
+  }
+  if (!(md.e_radius[1] > 0.0)) return CELESTE_EINVAL;
+  CK(cudaSetDevice(device));
+  celeste_ctx* c = new celeste_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->n_exp = m->n_exp;
+  c->n_dev = m->n_dev;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&c->d_model, sizeof(ModelDev)) != cudaSuccess ||
+      cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemcpy(c->d_model, &md, sizeof(md), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+    cudaFree(c->d_model);
+    cudaFree(c->d_err);
+    delete c;
+    return CELESTE_ECUDA;
+  }
+  *out = c;
+  return CELESTE_OK;
+}
+
+int celeste_destroy(celeste_ctx* c) {
+  if (!c) return CELESTE_EINVAL;
+  cudaSetDevice(c->device);
+  cudaFree(c->d_model);
+  cudaFree(c->d_err);
+  delete c;
+  return CELESTE_OK;
+}
+
+int celeste_synchronize(celeste_ctx* c, uint32_t* device_error) {
+  if (!c) return CELESTE_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned int w = 0;
+  CK(cudaMemcpy(&w, c->d_err, sizeof(w), cudaMemcpyDeviceToHost));
+  if (device_error) *device_error = w;
+  if (w) {
+    CK(cudaMemset(c->d_err, 0, sizeof(unsigned int)));
+    return CELESTE_EDEVICE;
+  }
+  return CELESTE_OK;
+}
+
+int64_t celeste_launch_count(const celeste_ctx* c) { return c ? c->launches : -1; }
+
+int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t* ids, int32_t n,
+                        const celeste_tuning* tuning, celeste_plan** out) {
+  if (!c || !pr || !out || n < 0 || (n > 0 && !ids)) return CELESTE_EINVAL;
+  *out = nullptr;
+  if (!pr->h_patch_ptr || !pr->h_patches || !pr->h_images || !pr->h_nbr_ptr ||
+      (pr->n_nbr > 0 && !pr->h_nbr_idx) || !pr->pixels || !pr->sky || !pr->images || !pr->theta)
+    return CELESTE_EINVAL;
+  const int ppi = tuning && tuning->pixels_per_item > 0 ? tuning->pixels_per_item : 256;
+  if (ppi < 32 || ppi > 65536) return CELESTE_EINVAL;
+  std::vector<char> seen(pr->n_sources, 0);
+  for (int j = 0; j < n; ++j) {
+    if (ids[j] < 0 || ids[j] >= pr->n_sources || seen[ids[j]]) return CELESTE_EINVAL;
+    seen[ids[j]] = 1;
+  }
+  std::vector<PairInfo> pairs;
+  std::vector<int32_t> slot_ptr(n + 1, 0), pair_nbr;
+  std::vector<Item> items;
+  int64_t bg = 0, visits = 0;
+  auto patch_ok = [&](const celeste_patch& q) {
+    if (q.image < 0 || q.image >= pr->n_images) return false;
+    const celeste_image& im = pr->h_images[q.image];
+    return q.w > 0 && q.h > 0 && q.x0 >= 0 && q.y0 >= 0 && q.x0 + q.w <= im.width &&
+           q.y0 + q.h <= im.height;
+  };
+  // own pairs
+  for (int j = 0; j < n; ++j) {
+    const int s = ids[j];
+    for (int q = pr->h_patch_ptr[s]; q < pr->h_patch_ptr[s + 1]; ++q) {
+      const celeste_patch& P = pr->h_patches[q];
+      if (!patch_ok(P)) return CELESTE_EINVAL;
+      const celeste_image& im = pr->h_images[P.image];
+      PairInfo pi{};
+      pi.source = s;
+      pi.slot = j;
+      pi.patch = q;
+      pi.image = P.image;
+      pi.x0 = P.x0;
+      pi.y0 = P.y0;
+      pi.w = P.w;
+      pi.h = P.h;
+      pi.pix_base = im.pix_offset + (int64_t)P.y0 * im.row_stride + P.x0;
+      pi.stride = im.row_stride;
+      pi.band = im.band;
+      pi.bg_base = bg;
+      const int area = P.w * P.h;
+      bg += area;
+      visits += area;
+      pi.item_begin = (int)items.size();
+      for (int st = 0; st < area; st += ppi) items.push_back(Item{(int)pairs.size(), st, std::min(ppi, area - st), 0});
+      pi.item_end = (int)items.size();
+      pairs.push_back(pi);
+    }
+    slot_ptr[j + 1] = (int)pairs.size();
+  }
+  const int n_own = (int)pairs.size();
+  // neighbour pairs: (neighbour source, its patch in the same image) that
+  // overlap an own patch
+  std::unordered_map<int64_t, int> nb_index;
+  for (int pp = 0; pp < n_own; ++pp) {
+    PairInfo& pi = pairs[pp];
+    pi.nbr_begin = (int)pair_nbr.size();
+    const int s = pi.source;
+    for (int k = pr->h_nbr_ptr[s]; k < pr->h_nbr_ptr[s + 1]; ++k) {
+      const int t = pr->h_nbr_idx[k];
+      if (t < 0 || t >= pr->n_sources) return CELESTE_EINVAL;
+      for (int q = pr->h_patch_ptr[t]; q < pr->h_patch_ptr[t + 1]; ++q) {
+        const celeste_patch& P = pr->h_patches[q];
+        if (P.image != pi.image) continue;
+        if (!patch_ok(P)) return CELESTE_EINVAL;
+        if (P.x0 >= pi.x0 + pi.w || pi.x0 >= P.x0 + P.w || P.y0 >= pi.y0 + pi.h || pi.y0 >= P.y0 + P.h)
+          continue;
+        const int64_t key = (int64_t)t * (int64_t)pr->n_patches + q;
+        auto it = nb_index.find(key);
+        int idx;
+        if (it == nb_index.end()) {
+          idx = (int)pairs.size();
+          nb_index.emplace(key, idx);
+          const celeste_image& im = pr->h_images[P.image];
+          PairInfo qn{};
+          qn.source = t;
+          qn.slot = -1;
+          qn.patch = q;
+          qn.image = P.image;
+          qn.x0 = P.x0;
+          qn.y0 = P.y0;
+          qn.w = P.w;
+          qn.h = P.h;
+          qn.pix_base = im.pix_offset + (int64_t)P.y0 * im.row_stride + P.x0;
+          qn.stride = im.row_stride;
+          qn.band = im.band;
+          qn.bg_base = -1;
+          qn.nbr_begin = qn.nbr_end = 0;
+          qn.item_begin = qn.item_end = 0;
+          pairs.push_back(qn);
+          // pairs may have been reallocated
+        } else {
+          idx = it->second;
+        }
+        pair_nbr.push_back(idx);
+      }
+    }
+    pairs[pp].nbr_end = (int)pair_nbr.size();
+  }
+
+  celeste_plan* p = new celeste_plan();
+  p->ctx = c;
+  p->visits = visits;
+  if (tuning) p->tuning = *tuning;
+  p->tuning.pixels_per_item = ppi;
+  int err = CELESTE_OK;
+  PlanView& v = p->v;
+  v.pixels = pr->pixels;
+  v.sky = pr->sky;
+  v.images = pr->images;
+  v.theta = pr->theta;
+  v.n = n;
+  v.n_pairs = (int)pairs.size();
+  v.n_own_pairs = n_own;
+  v.n_items = (int)items.size();
+  v.n_bg = bg;
+  v.err = c->d_err;
+  p->d_patches = pr->patches;
+  int32_t* d_ids = dev_alloc<int32_t>(p, n, &err);
+  PairInfo* d_pairs = dev_alloc<PairInfo>(p, pairs.size(), &err);
+  int32_t* d_nbr = dev_alloc<int32_t>(p, pair_nbr.size(), &err);
+  int32_t* d_slot = dev_alloc<int32_t>(p, n + 1, &err);
+  Item* d_items = dev_alloc<Item>(p, items.size(), &err);
+  v.records = dev_alloc<float>(p, pairs.size() * (size_t)kRecF, &err);
+  v.bg = dev_alloc<float2>(p, (size_t)bg, &err);
+  v.partials = dev_alloc<float>(p, items.size() * (size_t)kAcc, &err);
+  v.vpartials = dev_alloc<float>(p, items.size() * 2, &err);
+  v.theta_trial = dev_alloc<double>(p, (size_t)n * kTheta, &err);
+  v.step = dev_alloc<double>(p, (size_t)n * kTheta, &err);
+  v.pred = dev_alloc<double>(p, n, &err);
+  v.elbo_rel = dev_alloc<double>(p, n, &err);
+  p->rel_trial = dev_alloc<double>(p, n, &err);
+  v.grad = dev_alloc<double>(p, (size_t)n * kTheta, &err);
+  v.hess = dev_alloc<double>(p, (size_t)n * kTheta * kTheta, &err);
+  v.active = dev_alloc<uint8_t>(p, n, &err);
+  if (err != CELESTE_OK) {
+    celeste_plan_destroy(p);
+    return err;
+  }
+  cudaError_t ce = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes && ce == cudaSuccess) ce = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cp(d_ids, ids, n * sizeof(int32_t));
+  cp(d_pairs, pairs.data(), pairs.size() * sizeof(PairInfo));
+  cp(d_nbr, pair_nbr.data(), pair_nbr.size() * sizeof(int32_t));
+  cp(d_slot, slot_ptr.data(), (n + 1) * sizeof(int32_t));
+  cp(d_items, items.data(), items.size() * sizeof(Item));
+  if (ce == cudaSuccess) ce = cudaMemset(v.theta_trial, 0, (size_t)n * kTheta * sizeof(double));
+  if (ce == cudaSuccess) ce = cudaMemset(v.active, 1, n > 0 ? n : 1);
+  if (ce != cudaSuccess) {
+    celeste_plan_destroy(p);
+    return CELESTE_ECUDA;
+  }
+  v.src_ids = d_ids;
+  v.pairs = d_pairs;
+  v.pair_nbr = d_nbr;
+  v.slot_pair_ptr = d_slot;
+  v.items = d_items;
+  *out = p;
+  return CELESTE_OK;
+}
+
+int celeste_plan_destroy(celeste_plan* p) {
+  if (!p) return CELESTE_EINVAL;
+  for (void* a : p->allocs) cudaFree(a);
+  delete p;
+  return CELESTE_OK;
+}
+
+int64_t celeste_plan_visits(const celeste_plan* p) { return p ? p->visits : -1; }
+
+static int eval_common(celeste_ctx* c, celeste_plan* p, bool derivs) {
+  Launch L = make_launch(c, p);
+  CK(cudaMemsetAsync(p->v.active, 1, p->v.n > 0 ? p->v.n : 1, c->stream));
+  int rc = run_setup(c, p, 0, p->v.n_pairs, false);
+  if (rc) return rc;
+  c->launches += 2;
+  CK(launch_background(L, p->v));
+  CK(derivs ? launch_pixels_derivs(L, p->v) : launch_pixels_value(L, p->v));
+  return CELESTE_OK;
+}
+
+int celeste_elbo_grad_hess(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel,
+                           double* grad, double* hess) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c || !elbo || !grad || !hess) return CELESTE_EINVAL;
+  int rc = eval_common(c, p, true);
+  if (rc) return rc;
+  Launch L = make_launch(c, p);
+  ++c->launches;
+  return to_status(launch_epilogue(L, p->v, c->d_model, elbo, elbo_rel, grad, hess));
+}
+
+int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c) return CELESTE_EINVAL;
+  int rc = eval_common(c, p, false);
+  if (rc) return rc;
+  Launch L = make_launch(c, p);
+  ++c->launches;
+  return to_status(launch_epilogue_value(L, p->v, c->d_model, elbo, elbo_rel, false));
+}
+
+int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, int32_t* status,
+                        double* elbo_rel) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c || !delta || !status) return CELESTE_EINVAL;
+  if (p->v.n == 0) return CELESTE_OK;
+  Launch L = make_launch(c, p);
+  PlanView& v = p->v;
+  c->launches += 1;
+  CK(launch_mark_active(L, v, status));
+  int rc = run_setup(c, p, 0, v.n_pairs, false);
+  if (rc) return rc;
+  c->launches += 3;
+  CK(launch_background(L, v));
+  CK(launch_pixels_derivs(L, v));
+  CK(launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess));
+  if (elbo_rel) CK(cudaMemcpyAsync(elbo_rel, v.elbo_rel, v.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  c->launches += 1;
+  CK(launch_tr_step(L, v, delta, status));
+  rc = run_setup(c, p, 0, v.n_own_pairs, true);
+  if (rc) return rc;
+  c->launches += 3;
+  CK(launch_pixels_value(L, v));
+  CK(launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true));
+  CK(launch_tr_accept(L, v, p->rel_trial, delta, status));
+  return CELESTE_OK;
+}
+
+int celeste_tr_subproblem(celeste_ctx* c, int32_t n, const double* g, const double* H,
+                          const double* delta, double* p, double* pred) {
+  if (!c || n < 0 || (n > 0 && (!g || !H || !delta || !p || !pred))) return CELESTE_EINVAL;
+  Launch L = make_launch(c, nullptr);
+  ++c->launches;
+  return to_status(launch_tr_subproblem(L, n, g, H, delta, p, pred));
+}
+
+int celeste_render(celeste_ctx* c, const celeste_plan* pc, float* E_out, float* V_out) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c || (!E_out && !V_out) || !p->d_patches) return CELESTE_EINVAL;
+  Launch L = make_launch(c, p);
+  CK(cudaMemsetAsync(p->v.active, 1, p->v.n > 0 ? p->v.n : 1, c->stream));
+  int rc = run_setup(c, p, 0, p->v.n_own_pairs, false);
+  if (rc) return rc;
+  ++c->launches;
+  return to_status(launch_render(L, p->v, E_out, V_out, p->d_patches));
+}
+
+int celeste_background(celeste_ctx* c, const celeste_plan* pc, float* bgE, float* bgV) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c || (!bgE && !bgV) || !p->d_patches) return CELESTE_EINVAL;
+  Launch L = make_launch(c, p);
+  CK(cudaMemsetAsync(p->v.active, 1, p->v.n > 0 ? p->v.n : 1, c->stream));
+  int rc = run_setup(c, p, 0, p->v.n_pairs, false);
+  if (rc) return rc;
+  c->launches += 2;
+  CK(launch_background(L, p->v));
+  return to_status(launch_background_out(L, p->v, bgE, bgV, p->d_patches));
+}
+
+int celeste_color_sources(int32_t n, const int32_t* nbr_ptr, const int32_t* nbr_idx,
+                          int32_t* color) {
+  if (n < 0 || (n > 0 && (!nbr_ptr || !color))) return CELESTE_EINVAL;
+  int n_colors = 0;
+  std::vector<char> used;
+  for (int s = 0; s < n; ++s) {
+    used.assign(n_colors + 1, 0);
+    for (int k = nbr_ptr[s]; k < nbr_ptr[s + 1]; ++k) {
+      const int t = nbr_idx[k];
+      if (t < 0 || t >= n) return CELESTE_EINVAL;
+      if (t < s && color[t] <= n_colors) used[color[t]] = 1;
+    }
+    int col = 0;
+    while (used[col]) ++col;
+    color[s] = col;
+    n_colors = std::max(n_colors, col + 1);
+  }
+  return n_colors;
+}
+
+}  // extern "C"

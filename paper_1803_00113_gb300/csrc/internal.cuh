@@ -1,0 +1,174 @@
+// Library-internal declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/celeste.h"
+
+namespace celeste {
+
+constexpr int kTheta = CELESTE_N_THETA;
+constexpr int kPsf = CELESTE_N_PSF;
+constexpr int kMaxProf = CELESTE_MAX_PROFILE;
+constexpr int kMaxColor = CELESTE_MAX_COLOR;
+
+// ---- per-pair record written by the setup kernel -----------------------
+// A "pair" is (source, image patch).  Its record is a header of brightness
+// coefficients followed by one 8-float entry per Gaussian component:
+// 3 star components, then per PSF component k: n_exp exponential-profile and
+// n_dev de Vaucouleurs components.  Positions are local to the patch origin.
+constexpr int kHdr = 16;
+constexpr int kCompF = 8;
+constexpr int kMaxComp = kPsf * (1 + 2 * kMaxProf);          // 51
+constexpr int kRecF = kHdr + kMaxComp * kCompF;                // 424 floats
+// header slots
+enum : int {
+  H_CE0 = 0, H_CE1, H_CM0, H_CM1, H_K0, H_K1, H_EV0, H_EV1, H_Q0, H_Q1, H_RHO, H_RHO1
+};
+// component slots: mean x, mean y (local), precision P11, P12, P22,
+// log2(weight / (2 pi sqrt(det C))), tau (0 for the star), unused
+enum : int { C_MX = 0, C_MY, C_P11, C_P12, C_P22, C_LW, C_TAU };
+
+// ---- accumulators of one (pair, tile) work item ------------------------
+// w = (cE0, cE1, cM0, cM1, mu_x, mu_y, g11, g12, g22, rho): the per-image
+// natural coordinates.  Layout: value_rel, value_base, grad[10], then the
+// upper triangle of the Hessian (row-major, j <= k) without the three
+// (cM, cM) entries, which vanish identically.
+constexpr int kW = 10;
+constexpr int kAcc = 64;
+__host__ __device__ constexpr int hidx(int j, int k) {
+  // packed upper triangle (row-major, j <= k) of the 10 x 10 Hessian, minus
+  // the entries (2,2), (2,3) and (3,3), which are never stored
+  return 12 + (j * kW - (j * (j - 1)) / 2 + (k - j)) - (j == 2 ? 2 : (j >= 3 ? 3 : 0));
+}
+
+struct PairInfo {
+  int32_t source;      // source id
+  int32_t slot;        // plan slot of the owning source, -1 for neighbour pairs
+  int32_t patch;
+  int32_t image;
+  int32_t x0, y0, w, h;
+  int64_t pix_base;    // index of pixel (x0, y0) in the pixel pool
+  int32_t stride;
+  int32_t band;
+  int64_t bg_base;     // own pairs: offset in the plan's background pool
+  int32_t nbr_begin, nbr_end;  // own pairs: neighbour pairs in pair_nbr[]
+  int32_t item_begin, item_end;
+};
+
+struct Item {
+  int32_t pair;
+  int32_t start;
+  int32_t count;
+  int32_t pad;
+};
+
+struct ModelDev {
+  int32_t n_exp, n_dev, n_color, pad;
+  double alpha_exp[kMaxProf], tau_exp[kMaxProf], alpha_dev[kMaxProf], tau_dev[kMaxProf];
+  double prior_a;
+  double prior_r[2][2];
+  double color_w[2][kMaxColor];
+  double color_mean[2][kMaxColor][4];
+  double color_prec[2][kMaxColor][4][4];   // inverse covariances
+  double color_logdet[2][kMaxColor];
+  double e_radius[2], e_profile[2], e_axis[2];
+};
+
+// Everything a kernel needs about a plan, by value.
+struct PlanView {
+  const float* pixels;
+  const float* sky;
+  const celeste_image* images;
+  double* theta;              // problem theta [n_sources][27]
+  const int32_t* src_ids;     // [n] plan slot -> source id
+  const PairInfo* pairs;      // [n_pairs]: own pairs first
+  const int32_t* pair_nbr;    // neighbour pair indices per own pair
+  const int32_t* slot_pair_ptr;  // [n+1] own pairs per slot
+  const Item* items;          // [n_items]
+  float* records;             // [n_pairs][kRecF]
+  float2* bg;                 // [n_bg] background (E, V) per own patch pixel
+  float* partials;            // [n_items][kAcc]
+  float* vpartials;           // [n_items][2]
+  double* theta_trial;        // [n][27]
+  double* step;               // [n][27]
+  double* pred;               // [n]
+  double* elbo_rel;           // [n] value at the current iterate
+  double* grad;               // [n][27] scratch for newton_step
+  double* hess;               // [n][27][27]
+  uint8_t* active;            // [n] 1 if the slot takes part in the evaluation
+  unsigned int* err;          // device error word
+  int32_t n, n_pairs, n_own_pairs, n_items;
+  int64_t n_bg;
+};
+
+struct Launch {
+  cudaStream_t stream;
+  int sm_count;
+  int warps_per_block;
+  int blocks_per_sm;
+  int pixels_per_item;
+  int n_exp, n_dev;
+};
+
+// ---- kernel launchers (one per translation unit) ------------------------
+// setup.cu: per-pair records; own pairs read theta_trial when use_trial.
+cudaError_t launch_setup(const Launch& L, const PlanView& v, const ModelDev* model,
+                         int first_pair, int n_pairs, bool use_trial);
+// pixel.cu
+cudaError_t launch_background(const Launch& L, const PlanView& v);
+cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v);
+cudaError_t launch_pixels_value(const Launch& L, const PlanView& v);
+cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, float* V_out,
+                          const celeste_patch* patches);
+cudaError_t launch_background_out(const Launch& L, const PlanView& v, float* bgE, float* bgV,
+                                  const celeste_patch* patches);
+// epilogue.cu
+cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* model,
+                            double* elbo, double* elbo_rel, double* grad, double* hess);
+cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
+                                  double* elbo, double* elbo_rel, bool use_trial);
+// newton.cu
+cudaError_t launch_tr_step(const Launch& L, const PlanView& v, const double* delta,
+                           int32_t* status);
+cudaError_t launch_tr_accept(const Launch& L, const PlanView& v, const double* rel_trial,
+                             double* delta, int32_t* status);
+cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const double* H,
+                                 const double* delta, double* p, double* pred);
+cudaError_t launch_mark_active(const Launch& L, const PlanView& v, const int32_t* status);
+
+// ---- small device helpers ----------------------------------------------
+__device__ __forceinline__ void set_error(unsigned int* err, unsigned int bit) {
+  atomicOr(err, bit);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Bilinear sky at pixel (x, y) of image `im` (knots span the image).
+__device__ __forceinline__ float sky_value(const celeste_image& im, const float* sky, float x,
+                                           float y) {
+  const float* k = sky + im.sky_offset;
+  const int nx = im.sky_nx, ny = im.sky_ny;
+  if (nx == 1 && ny == 1) return k[0];
+  float gx = nx > 1 ? x * (float)(nx - 1) / (float)max(im.width - 1, 1) : 0.f;
+  float gy = ny > 1 ? y * (float)(ny - 1) / (float)max(im.height - 1, 1) : 0.f;
+  int ix = min(max((int)floorf(gx), 0), max(nx - 2, 0));
+  int iy = min(max((int)floorf(gy), 0), max(ny - 2, 0));
+  float fx = gx - (float)ix, fy = gy - (float)iy;
+  int ix1 = min(ix + 1, nx - 1), iy1 = min(iy + 1, ny - 1);
+  float a = k[iy * nx + ix], b = k[iy * nx + ix1], c = k[iy1 * nx + ix], d = k[iy1 * nx + ix1];
+  return (1.f - fy) * ((1.f - fx) * a + fx * b) + fy * ((1.f - fx) * c + fx * d);
+}
+
+}  // namespace celeste

@@ -1,0 +1,489 @@
+// Pixel kernels: the hot loop of the method.
+//
+// For every (source, image patch, pixel tile) work item, one warp stages the
+// pair's component record in shared memory and each lane walks its pixels:
+//   * renders the source's galaxy and star profile densities with their
+//     first and second derivatives in the image's natural coordinates
+//     (centre mu, shape G = A Sigma_s A^T, profile weight rho) -- Sec. 2.2.3;
+//   * forms E = bgE + E_s and V = bgV + V_s (Eqs. conditional, vareq) and the
+//     delta-method pixel term -E + x (log E - V / (2 E^2)) (Eq. eq:log_p_last,
+//     Sec. 4.2.2) with its partials;
+//   * accumulates the value, the gradient and the Hessian over the 10
+//     per-image natural coordinates w = (cE0, cE1, cM0, cM1, mu, G, rho).
+// The warp reduces its 64 sums with shuffles and writes them to the item's
+// slot; the epilogue chains them to the 27 coordinates in FP64.
+//
+// Derivatives of a Gaussian component with respect to its covariance come
+// from the heat equation (d phi / dC_ab = 1/2 d^2 phi / dmu_a dmu_b), so the
+// kernel only needs the Hermite polynomials of orders 0..4 in y = P (p - mu).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace celeste {
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
+
+// Sums over the components of one galaxy profile (weights without rho):
+// S*: derivatives in mu; T2: tau-weighted second order (-> dG);
+// T3: tau-weighted third order (-> d mu dG); T4: tau^2 fourth order (-> dG dG).
+struct GalSums {
+  float s0, s1x, s1y, s2xx, s2xy, s2yy;
+  float t2xx, t2xy, t2yy;
+  float t3a, t3b, t3c, t3d;            // 111, 112, 122, 222
+  float t4a, t4b, t4c, t4d, t4e;       // 1111, 1112, 1122, 1222, 2222
+};
+
+__device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, float px, float py,
+                                               GalSums& g) {
+  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22], tau = c[C_TAU];
+  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const float y1 = fmaf(P11, dx, P12 * dy);
+  const float y2 = fmaf(P12, dx, P22 * dy);
+  const float Q = fmaf(dx, y1, dy * y2);
+  const float phi = exp2f(fmaf(-kHalfLog2e, Q, c[C_LW]));
+  const float h11 = fmaf(y1, y1, -P11);
+  const float h12 = fmaf(y1, y2, -P12);
+  const float h22 = fmaf(y2, y2, -P22);
+  const float pt = phi * tau;
+  const float pt2 = pt * tau;
+  g.s0 += phi;
+  g.s1x = fmaf(phi, y1, g.s1x);
+  g.s1y = fmaf(phi, y2, g.s1y);
+  g.s2xx = fmaf(phi, h11, g.s2xx);
+  g.s2xy = fmaf(phi, h12, g.s2xy);
+  g.s2yy = fmaf(phi, h22, g.s2yy);
+  g.t2xx = fmaf(pt, h11, g.t2xx);
+  g.t2xy = fmaf(pt, h12, g.t2xy);
+  g.t2yy = fmaf(pt, h22, g.t2yy);
+  // third order: y_a y_b y_c - (P_ab y_c + P_ac y_b + P_bc y_a)
+  const float P12x2 = 2.f * P12;
+  g.t3a = fmaf(pt, y1 * fmaf(-2.f, P11, h11), g.t3a);
+  g.t3b = fmaf(pt, fmaf(y2, h11, -P12x2 * y1), g.t3b);
+  g.t3c = fmaf(pt, fmaf(y1, h22, -P12x2 * y2), g.t3c);
+  g.t3d = fmaf(pt, y2 * fmaf(-2.f, P22, h22), g.t3d);
+  // fourth order, written with h = y y^T - P
+  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), -2.f * P11 * P11), g.t4a);
+  g.t4b = fmaf(pt2, fmaf(h12, fmaf(-2.f, P11, h11), -P12x2 * (h11 + P11)), g.t4b);
+  g.t4c = fmaf(pt2, fmaf(h11, h22, -P12x2 * fmaf(2.f, h12, P12)), g.t4c);
+  g.t4d = fmaf(pt2, fmaf(h12, fmaf(-2.f, P22, h22), -P12x2 * (h22 + P22)), g.t4d);
+  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), -2.f * P22 * P22), g.t4e);
+}
+
+__device__ __forceinline__ float gauss_value(const float* __restrict__ c, float px, float py) {
+  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
+  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const float y1 = fmaf(P11, dx, P12 * dy);
+  const float y2 = fmaf(P12, dx, P22 * dy);
+  const float Q = fmaf(dx, y1, dy * y2);
+  return exp2f(fmaf(-kHalfLog2e, Q, c[C_LW]));
+}
+
+// Galaxy (rho-mixed) and star profile densities of one pair at a pixel.
+__device__ __forceinline__ void profiles_value(const float* __restrict__ rec, int ne, int nd,
+                                               float px, float py, float& F0, float& F1) {
+  float fs = 0.f, fe = 0.f, fd = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPsf; ++k) fs += gauss_value(rec + kHdr + k * kCompF, px, py);
+  const int per = ne + nd;
+  for (int k = 0; k < kPsf; ++k) {
+    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
+    for (int j = 0; j < ne; ++j) fe += gauss_value(base + j * kCompF, px, py);
+    for (int j = 0; j < nd; ++j) fd += gauss_value(base + (ne + j) * kCompF, px, py);
+  }
+  F0 = fmaf(rec[H_RHO], fe, rec[H_RHO1] * fd);
+  F1 = fs;
+}
+
+// The source's own E_q[l f] and V_q[l f] at a pixel.  V uses the
+// cancellation-free form sum_i q_i ev_i (k_i F_i)^2 + q0 q1 (k0 F0 - k1 F1)^2.
+__device__ __forceinline__ void own_moments(const float* __restrict__ rec, float F0, float F1,
+                                            float& Es, float& Vs) {
+  const float k0F = rec[H_K0] * F0, k1F = rec[H_K1] * F1;
+  Es = fmaf(rec[H_CE0], F0, rec[H_CE1] * F1);
+  const float d = k0F - k1F;
+  Vs = fmaf(rec[H_Q0] * rec[H_EV0] * k0F, k0F,
+            fmaf(rec[H_Q1] * rec[H_EV1] * k1F, k1F, rec[H_Q0] * rec[H_Q1] * d * d));
+}
+
+// One pixel: render with derivatives and accumulate value, gradient, Hessian.
+__device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int ne, int nd,
+                                             float px, float py, float x, float2 bg,
+                                             float* __restrict__ acc) {
+  // ---- star: value, d mu, d mu d mu
+  float F1 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPsf; ++k) {
+    const float* c = rec + kHdr + k * kCompF;
+    const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
+    const float dx = px - c[C_MX], dy = py - c[C_MY];
+    const float y1 = fmaf(P11, dx, P12 * dy);
+    const float y2 = fmaf(P12, dx, P22 * dy);
+    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
+    F1 += phi;
+    sx = fmaf(phi, y1, sx);
+    sy = fmaf(phi, y2, sy);
+    sxx = fmaf(phi, fmaf(y1, y1, -P11), sxx);
+    sxy = fmaf(phi, fmaf(y1, y2, -P12), sxy);
+    syy = fmaf(phi, fmaf(y2, y2, -P22), syy);
+  }
+  // ---- galaxy: exponential and de Vaucouleurs sums
+  GalSums ge = {}, gd = {};
+  const int per = ne + nd;
+  for (int k = 0; k < kPsf; ++k) {
+    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
+    for (int j = 0; j < ne; ++j) gal_accumulate(base + j * kCompF, px, py, ge);
+    for (int j = 0; j < nd; ++j) gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
+  }
+  const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
+#define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
+  // galaxy density and its derivatives over (mu_x, mu_y, g11, g12, g22, rho)
+  const float F0 = MIX(s0);
+  float d0[6], h0[6][6];
+  d0[0] = MIX(s1x);
+  d0[1] = MIX(s1y);
+  d0[2] = 0.5f * MIX(t2xx);
+  d0[3] = MIX(t2xy);
+  d0[4] = 0.5f * MIX(t2yy);
+  d0[5] = ge.s0 - gd.s0;
+  h0[0][0] = MIX(s2xx);
+  h0[0][1] = MIX(s2xy);
+  h0[1][1] = MIX(s2yy);
+  h0[0][2] = 0.5f * MIX(t3a);
+  h0[1][2] = 0.5f * MIX(t3b);
+  h0[0][3] = MIX(t3b);
+  h0[1][3] = MIX(t3c);
+  h0[0][4] = 0.5f * MIX(t3c);
+  h0[1][4] = 0.5f * MIX(t3d);
+  h0[2][2] = 0.25f * MIX(t4a);
+  h0[2][3] = 0.5f * MIX(t4b);
+  h0[2][4] = 0.25f * MIX(t4c);
+  h0[3][3] = MIX(t4c);
+  h0[3][4] = 0.5f * MIX(t4d);
+  h0[4][4] = 0.25f * MIX(t4e);
+  h0[0][5] = ge.s1x - gd.s1x;
+  h0[1][5] = ge.s1y - gd.s1y;
+  h0[2][5] = 0.5f * (ge.t2xx - gd.t2xx);
+  h0[3][5] = ge.t2xy - gd.t2xy;
+  h0[4][5] = 0.5f * (ge.t2yy - gd.t2yy);
+  h0[5][5] = 0.f;
+#undef MIX
+
+  // ---- moments and the pixel term
+  const float cE0 = rec[H_CE0], cE1 = rec[H_CE1], cM0 = rec[H_CM0], cM1 = rec[H_CM1];
+  float Es, Vs;
+  own_moments(rec, F0, F1, Es, Vs);
+  const float bgE = bg.x, bgV = bg.y;
+  const float E = bgE + Es, V = bgV + Vs;
+  const float r = __frcp_rn(E);
+  const float rb = __frcp_rn(bgE);
+  const float xr = x * r;
+  const float xr2 = xr * r;        // x / E^2
+  const float xr3 = xr2 * r;       // x / E^3
+  const float TE = fmaf(x - E, r, xr3 * V);
+  const float TV = -0.5f * xr2;
+  const float TEE = fmaf(-3.f * xr3 * r, V, -xr2);
+  const float TEV = xr3;
+  const float tE = fmaf(-2.f * Es, TV, TE);
+  const float tM = TV;
+  const float tEE = fmaf(-4.f * Es, TEV, fmaf(-2.f, TV, TEE));
+  const float tEM = TEV;
+
+  acc[0] += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bgV * rb * rb, -Es);
+  acc[1] += fmaf(x, __logf(bgE) - 0.5f * bgV * rb * rb, -bgE);
+
+  // gradient vectors of E_s (a) and M_s (b) over the six geometric coordinates
+  float aG[6], bG[6];
+  const float m0 = 2.f * cM0 * F0, m1 = 2.f * cM1 * F1;
+  aG[0] = fmaf(cE0, d0[0], cE1 * sx);
+  aG[1] = fmaf(cE0, d0[1], cE1 * sy);
+  bG[0] = fmaf(m0, d0[0], m1 * sx);
+  bG[1] = fmaf(m0, d0[1], m1 * sy);
+#pragma unroll
+  for (int g = 2; g < 6; ++g) {
+    aG[g] = cE0 * d0[g];
+    bG[g] = m0 * d0[g];
+  }
+  const float F0s = F0 * F0, F1s = F1 * F1;
+  // gradient over w
+  acc[2] = fmaf(tE, F0, acc[2]);
+  acc[3] = fmaf(tE, F1, acc[3]);
+  acc[4] = fmaf(tM, F0s, acc[4]);
+  acc[5] = fmaf(tM, F1s, acc[5]);
+#pragma unroll
+  for (int g = 0; g < 6; ++g) acc[6 + g] = fmaf(tE, aG[g], fmaf(tM, bG[g], acc[6 + g]));
+
+  // Hessian: tEE a a^T + tEM (a b^T + b a^T) + tE d2E_s + tM d2M_s
+  float u[6], cg[6];
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+    cg[g] = tEM * bG[g];
+    u[g] = fmaf(tEE, aG[g], cg[g]);
+  }
+  acc[hidx(0, 0)] = fmaf(tEE, F0s, acc[hidx(0, 0)]);
+  acc[hidx(0, 1)] = fmaf(tEE, F0 * F1, acc[hidx(0, 1)]);
+  acc[hidx(1, 1)] = fmaf(tEE, F1s, acc[hidx(1, 1)]);
+  acc[hidx(0, 2)] = fmaf(tEM * F0, F0s, acc[hidx(0, 2)]);
+  acc[hidx(0, 3)] = fmaf(tEM * F0, F1s, acc[hidx(0, 3)]);
+  acc[hidx(1, 2)] = fmaf(tEM * F1, F0s, acc[hidx(1, 2)]);
+  acc[hidx(1, 3)] = fmaf(tEM * F1, F1s, acc[hidx(1, 3)]);
+  const float tm2F0 = 2.f * tM * F0, tm2F1 = 2.f * tM * F1;
+  const float eF0 = tEM * F0s, eF1 = tEM * F1s;
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+    acc[hidx(0, 4 + g)] = fmaf(F0, u[g], fmaf(tE, d0[g], acc[hidx(0, 4 + g)]));
+    acc[hidx(2, 4 + g)] = fmaf(eF0, aG[g], fmaf(tm2F0, d0[g], acc[hidx(2, 4 + g)]));
+  }
+  acc[hidx(1, 4)] = fmaf(F1, u[0], fmaf(tE, sx, acc[hidx(1, 4)]));
+  acc[hidx(1, 5)] = fmaf(F1, u[1], fmaf(tE, sy, acc[hidx(1, 5)]));
+  acc[hidx(3, 4)] = fmaf(eF1, aG[0], fmaf(tm2F1, sx, acc[hidx(3, 4)]));
+  acc[hidx(3, 5)] = fmaf(eF1, aG[1], fmaf(tm2F1, sy, acc[hidx(3, 5)]));
+#pragma unroll
+  for (int g = 2; g < 6; ++g) {
+    acc[hidx(1, 4 + g)] = fmaf(F1, u[g], acc[hidx(1, 4 + g)]);
+    acc[hidx(3, 4 + g)] = fmaf(eF1, aG[g], acc[hidx(3, 4 + g)]);
+  }
+  const float D0 = fmaf(tE, cE0, tM * m0);   // dl/dF0 (direct part)
+  const float D1 = fmaf(tE, cE1, tM * m1);
+  const float q0 = 2.f * tM * cM0, q1 = 2.f * tM * cM1;
+  const float h1[2][2] = {{sxx, sxy}, {sxy, syy}};
+  const float d1[2] = {sx, sy};
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+#pragma unroll
+    for (int h = g; h < 6; ++h) {
+      float v = fmaf(aG[g], u[h], cg[g] * aG[h]);
+      v = fmaf(D0, h0[g][h], v);
+      v = fmaf(q0 * d0[g], d0[h], v);
+      if (g < 2 && h < 2) {
+        v = fmaf(D1, h1[g][h], v);
+        v = fmaf(q1 * d1[g], d1[h], v);
+      }
+      acc[hidx(4 + g, 4 + h)] += v;
+    }
+  }
+}
+
+// Writes the 64 warp-reduced sums of one item (lane a holds sums a, a + 32).
+__device__ __forceinline__ void reduce_store(float* __restrict__ acc, float* __restrict__ out,
+                                             int lane) {
+#pragma unroll
+  for (int a = 0; a < kAcc; ++a) acc[a] = warp_sum(acc[a]);
+#pragma unroll
+  for (int a = 0; a < kAcc; ++a)
+    if ((a & 31) == lane) out[a] = acc[a];
+}
+
+__device__ __forceinline__ void stage_record(float* __restrict__ dst, const float* __restrict__ src,
+                                             int lane) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int i = lane; i < kRecF / 4; i += 32) d4[i] = s4[i];
+}
+
+__global__ void __launch_bounds__(128) derivs_kernel(PlanView v, int ne, int nd) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (!v.active[pi.slot]) continue;
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    float acc[kAcc];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) acc[a] = 0.f;
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
+      const float2 bg = v.bg[pi.bg_base + q];
+      pixel_derivs(rec, ne, nd, (float)qx, (float)qy, x, bg, acc);
+    }
+    reduce_store(acc, v.partials + (size_t)it * kAcc, lane);
+  }
+}
+
+__global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (!v.active[pi.slot]) continue;
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    float rel = 0.f, base = 0.f;
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
+      const float2 bg = v.bg[pi.bg_base + q];
+      float F0, F1, Es, Vs;
+      profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
+      own_moments(rec, F0, F1, Es, Vs);
+      const float E = bg.x + Es, V = bg.y + Vs;
+      const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
+      rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
+      base += fmaf(x, __logf(bg.x) - 0.5f * bg.y * rb * rb, -bg.x);
+    }
+    rel = warp_sum(rel);
+    base = warp_sum(base);
+    if (lane == 0) {
+      v.vpartials[2 * (size_t)it] = rel;
+      v.vpartials[2 * (size_t)it + 1] = base;
+    }
+  }
+}
+
+// Background of every own patch pixel: sky plus each neighbour's E and V
+// where the pixel lies in that neighbour's patch (support rule, Sec. 2.2.3).
+__global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int nd) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (!v.active[pi.slot]) continue;
+    const celeste_image& im = v.images[pi.image];
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
+      if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
+      v.bg[pi.bg_base + q] = make_float2(s, 0.f);
+    }
+    for (int nb = pi.nbr_begin; nb < pi.nbr_end; ++nb) {
+      const int np = v.pair_nbr[nb];
+      const PairInfo qn = v.pairs[np];
+      __syncwarp();
+      stage_record(rec, v.records + (size_t)np * kRecF, lane);
+      __syncwarp();
+      for (int q = item.start + lane; q < end; q += 32) {
+        const int qy = q / pi.w;
+        const int gx = pi.x0 + (q - qy * pi.w), gy = pi.y0 + qy;
+        const int lx = gx - qn.x0, ly = gy - qn.y0;
+        if (lx < 0 || ly < 0 || lx >= qn.w || ly >= qn.h) continue;
+        float F0, F1, Es, Vs;
+        profiles_value(rec, ne, nd, (float)lx, (float)ly, F0, F1);
+        own_moments(rec, F0, F1, Es, Vs);
+        float2 b = v.bg[pi.bg_base + q];
+        b.x += Es;
+        b.y += Vs;
+        v.bg[pi.bg_base + q] = b;
+      }
+    }
+  }
+}
+
+// Own E_s and V_s of every plan pair, scattered to the caller's pool layout.
+__global__ void __launch_bounds__(128) render_kernel(PlanView v, int ne, int nd, float* E_out,
+                                                     float* V_out,
+                                                     const celeste_patch* __restrict__ patches) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    const int64_t off = patches[pi.patch].pool_offset;
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      float F0, F1, Es, Vs;
+      profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
+      own_moments(rec, F0, F1, Es, Vs);
+      if (E_out) E_out[off + q] = Es;
+      if (V_out) V_out[off + q] = Vs;
+    }
+  }
+}
+
+__global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
+                                  const celeste_patch* __restrict__ patches) {
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    const int64_t off = patches[pi.patch].pool_offset;
+    for (int q = item.start + lane; q < item.start + item.count; q += 32) {
+      const float2 b = v.bg[pi.bg_base + q];
+      if (bgE) bgE[off + q] = b.x;
+      if (bgV) bgV[off + q] = b.y;
+    }
+  }
+}
+
+static int grid_for(const Launch& L, int n_items, int wpb) {
+  int blocks = L.sm_count * (L.blocks_per_sm > 0 ? L.blocks_per_sm : 4);
+  const int needed = (n_items + wpb - 1) / wpb;
+  return blocks < needed ? blocks : (needed > 0 ? needed : 1);
+}
+
+static size_t smem_bytes(int wpb) { return (size_t)wpb * kRecF * sizeof(float); }
+
+constexpr int kWpb = 4;   // warps per block of the pixel kernels
+
+cudaError_t launch_background(const Launch& L, const PlanView& v) {
+  if (v.n_items == 0) return cudaSuccess;
+  background_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
+  if (v.n_items == 0) return cudaSuccess;
+  derivs_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pixels_value(const Launch& L, const PlanView& v) {
+  if (v.n_items == 0) return cudaSuccess;
+  value_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, float* V_out,
+                          const celeste_patch* patches) {
+  if (v.n_items == 0) return cudaSuccess;
+  render_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev, E_out, V_out, patches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_background_out(const Launch& L, const PlanView& v, float* bgE, float* bgV,
+                                  const celeste_patch* patches) {
+  if (v.n_items == 0) return cudaSuccess;
+  bg_scatter_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, 0, L.stream>>>(v, bgE, bgV,
+                                                                              patches);
+  return cudaGetLastError();
+}
+
+}  // namespace celeste
