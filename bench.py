@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark: source-pixel visits per second of the per-source ELBO with its
+gradient and Hessian, inside one trust-region Newton pass over a field.
+
+One step = one Newton trust-region iteration on every source of the field,
+colour class by colour class (sources of a class do not overlap, so they are
+updated together; the background of each class reflects the classes before
+it).  Each iteration evaluates L_s, its gradient and Hessian (the visits
+counted), solves the FP64 trust-region subproblem and evaluates the trial
+point.  Every timed step starts from the same parameters, so each one does
+the full work.
+
+Default workload: a field of five 2048 x 1489 images (one per band) with 600
+sources, 30 % stars (the shape of the paper's synthetic study set).  Inputs
+are seeded synthetic data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fields  # noqa: E402
+
+METRIC = "source-pixel visits/s (ELBO+grad+Hessian)"
+UNIT = "visits/s"
+# Algorithmic FP32 work of one visit in the derivative pixel kernel (value,
+# 10 first and 52 second derivatives over the per-image natural coordinates,
+# 48 galaxy + 3 star Gaussian components; FMA = 2 FLOP), counted from the
+# kernel's arithmetic as written.
+FLOP_PER_VISIT = 5320
+FP32_LANES_PER_SM = 128
+SEED = 1803_00113
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["field", "batched"], default="field")
+    ap.add_argument("--sources", type=int, default=0, help="override the source count")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args(argv)
+
+
+def workload(name, n_sources, seed):
+    if name == "field":
+        n = n_sources or 600
+        p = fields.single_field(seed=seed, n_sources=n)
+        cfg = {"workload": "single field: 5 bands x 1 image of 2048x1489 px, "
+                           f"{n} sources (30% stars), log-normal fluxes, one Newton "
+                           "trust-region pass in colour classes",
+               "bands": 5, "image_px": [2048, 1489], "sources": n}
+    else:
+        n = n_sources or 8192
+        p = fields.batched(seed=seed, n_sources=n)
+        cfg = {"workload": f"batched: {n} sources, patches 15..101 px, 1..6 images per band, "
+                           "0..10 neighbours, one Newton trust-region pass in colour classes",
+               "sources": n}
+    return p, cfg
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; sources shard with no exchange)
+# ---------------------------------------------------------------------------
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value, world, device="cpu"):
+    """Maximum of a float over ranks (the job's time is its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world, device="cpu"):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# the CPU baseline: the oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(problem, seconds, order=None):
+    import torch
+    import oracle
+    order = list(range(problem.n_sources)) if order is None else order
+    t_total, visits, used = 0.0, 0, []
+    for s in order:
+        t0 = time.perf_counter()
+        oracle.elbo_grad_hess(problem, s)
+        t_total += time.perf_counter() - t0
+        visits += problem.visits([s])
+        used.append(s)
+        if t_total >= seconds:
+            break
+    return {"value": visits / t_total, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle ELBO+gradient+Hessian of {len(used)} of the workload's "
+                      f"{problem.n_sources} sources ({visits} visits, {t_total:.1f} s)"}
+
+
+def traffic_per_launch(visits_per_launch):
+    """DRAM bytes per derivative-kernel launch from the committed ncu summary,
+    scaled by visits, when the summary was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "derivs_kernel_dram.json")
+    src = os.path.join(ROOT, "paper_1803_00113_gb300", "csrc", "pixel.cu")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("pixel_cu_sha256_16") != h:
+        return None
+    return d["dram_bytes_per_visit"] * visits_per_launch
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_info()
+    dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1803_00113_gb300 import build_lib
+    build_lib.build()
+    from paper_1803_00113_gb300 import celeste as cel
+
+    problem, cfg = workload(args.workload, args.sources, SEED + 1 + rank)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ctx = cel.Context(problem.model, device=local, stream=stream)
+        dp = cel.DeviceProblem(problem, dev)
+        classes = cel.color_classes(problem)
+        plans = [cel.Plan(ctx, dp, c) for c in classes]
+        visits = sum(p.visits for p in plans)
+        theta0 = dp.theta.clone()
+        delta, status = cel.newton_state(dp)
+        delta0, status0 = delta.clone(), status.clone()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+        def reset():
+            dp.theta.copy_(theta0)
+            delta.copy_(delta0)
+            status.copy_(status0)
+
+        def step():
+            for p in plans:
+                cel.newton_step(p, delta, status)
+
+        ctx.profile(True)
+        for _ in range(max(args.warmup, 1)):
+            reset()
+            step()
+        ctx.synchronize()
+        ctx.profile_read(reset=True)
+        graph = None
+        if not args.no_graph:
+            ctx.profile(True)
+            reset()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+            stream.synchronize()
+            for _ in range(2):
+                reset()
+                graph.replay()
+            ctx.synchronize()
+
+        def run_step():
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
+
+        # ---- timed region: K steps, L2 flushed between steps (outside the events)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = ctx.launches()
+        step_ms, kern_ms, kern_launch, kern_visits = [], 0.0, 0, 0
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            reset()
+            flush.zero_()
+            ev[k][0].record(stream)
+            run_step()
+            ev[k][1].record(stream)
+            if graph is not None:
+                stream.synchronize()
+                ms, nl, nv = ctx.profile_read(reset=False)
+                kern_ms += ms
+                kern_launch += nl
+                kern_visits += nv
+        torch.cuda.synchronize(dev)
+        if graph is None:
+            kern_ms, kern_launch, kern_visits = ctx.profile_read(reset=True)
+        n_launch = ctx.launches() - l0
+        if graph is not None:
+            # a replay launches the captured kernels: count them per step
+            n_launch = (ctx.launches() - l0) + args.steps * launches_per_step(plans)
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        ctx.synchronize()
+        barrier(world)
+        total_s = reduce_max(sum(step_ms) / 1e3, world, dev)
+        all_visits = reduce_sum(visits * args.steps, world, dev)
+        value = all_visits / total_s
+
+        # ---- end to end through the public API, host buffers
+        pin_pix = torch.from_numpy(problem.pixels).pin_memory()
+        pin_theta = torch.from_numpy(problem.theta.copy()).pin_memory()
+        out_theta = torch.empty_like(pin_theta).pin_memory()
+        h2d = pin_pix.numel() * 4 + pin_theta.numel() * 8
+        d2h = out_theta.numel() * 8
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for k in range(args.steps):
+            dp.pixels.copy_(pin_pix, non_blocking=True)
+            dp.theta.copy_(pin_theta, non_blocking=True)
+            delta.copy_(delta0)
+            status.copy_(status0)
+            run_step()
+            out_theta.copy_(dp.theta, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_s = reduce_max(e0.elapsed_time(e1) / 1e3, world, dev)
+        e2e_value = all_visits / e2e_s
+
+        # ---- the plain one-source-per-launch form (same kernels)
+        plain = None
+        if not args.no_plain and rank == 0:
+            single = [cel.Plan(ctx, dp, [s]) for s in range(problem.n_sources)]
+            reset()
+            for s in range(min(20, problem.n_sources)):
+                cel.newton_step(single[s], delta, status)
+            torch.cuda.synchronize(dev)
+            reset()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for c in classes:
+                for s in c:
+                    cel.newton_step(single[int(s)], delta, status)
+                    stream.synchronize()
+            plain_s = time.perf_counter() - t0
+            plain = {"value": visits / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
+                     "form": "one source per launch sequence, host sync after each source"}
+
+    # ---- roofline of the derivative pixel kernel
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    per_launch_visits = kern_visits / max(kern_launch, 1)
+    avg_ms = kern_ms / max(kern_launch, 1)
+    achieved = FLOP_PER_VISIT * per_launch_visits / (avg_ms / 1e3) / 1e12 if kern_launch else None
+    traffic = traffic_per_launch(per_launch_visits)
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded fields shaped like the paper's study set)",
+        "config": dict(cfg, l2="flushed between steps (256 MB write outside the timed events)",
+                       graph=graph is not None, visits_per_step=visits,
+                       colour_classes=len(classes)),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(n_launch),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "kernel": "derivs_kernel",
+                     "kernel_ms_per_launch": avg_ms, "visits_per_launch": per_launch_visits,
+                     "flop_per_visit": FLOP_PER_VISIT,
+                     "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                                   f"lanes x 2 FLOP x {sm_max:.0f} MHz"},
+        "plain_per_source": plain,
+    }
+    if plain:
+        line["vs_plain"] = value / plain["value"]
+    if not args.no_cpu_baseline and world == 1:
+        rng = np.random.default_rng(0)
+        line["cpu_baseline"] = cpu_baseline(problem, args.cpu_seconds,
+                                            list(rng.permutation(problem.n_sources)))
+    return line
+
+
+def launches_per_step(plans):
+    # per plan and Newton iteration: mark, setup, background, derivatives,
+    # epilogue, trust-region step, trial setup, trial value, trial epilogue, accept
+    return 10 * len(plans)
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    world, rank, local = dist_info()
+    if rank != 0:
+        return None
+    import torch
+    import oracle
+    problem, cfg = workload(args.workload, args.sources, SEED + 1)
+    rng = np.random.default_rng(0)
+    order = list(rng.permutation(problem.n_sources))
+    per_step = 2
+    times, visits = [], 0
+    k = 0
+    for i in range(args.warmup + args.steps):
+        srcs = [order[(k + j) % len(order)] for j in range(per_step)]
+        k += per_step
+        t0 = time.perf_counter()
+        for s in srcs:
+            oracle.elbo_grad_hess(problem, s)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            visits += problem.visits(srcs)
+    value = visits / sum(times)
+    sample = (f"each step: FP64 oracle ELBO+gradient+Hessian of {per_step} sources of the "
+              f"workload ({visits} visits over {args.steps} steps)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded fields shaped like the paper's study set)",
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    world = dist_info()[0]
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,18 @@ int celeste_destroy(celeste_ctx* ctx);
 int celeste_synchronize(celeste_ctx* ctx, uint32_t* device_error);
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t celeste_launch_count(const celeste_ctx* ctx);
+/* Event timing of the derivative pixel kernel (the dominant kernel of
+ * celeste_elbo_grad_hess and celeste_newton_step): when enabled, every
+ * launch is bracketed by a pair of CUDA events recorded on the context's
+ * stream (enabling also clears the list of pairs; events are reused).
+ * celeste_profile_read synchronises the stream and returns the summed
+ * kernel time (ms) over the recorded pairs, their number and the
+ * source-pixel visits they processed; reset != 0 clears the list.  A CUDA
+ * graph captured with timing enabled records the same pairs on every
+ * replay: read with reset = 0 after each replay. */
+int celeste_profile_enable(celeste_ctx* ctx, int on);
+int celeste_profile_read(celeste_ctx* ctx, int reset, double* total_ms, int64_t* launches,
+                         int64_t* visits);
 
 /* A plan binds a list of sources of a problem to a work decomposition
  * (per source, image and pixel tile) and owns the device scratch of the

@@ -72,6 +72,9 @@ def lib():
         "celeste_destroy": (ctypes.c_int, [P]),
         "celeste_synchronize": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32)]),
         "celeste_launch_count": (I64, [P]),
+        "celeste_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "celeste_profile_read": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(D),
+                                                ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "celeste_plan_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem), P, I32,
                                                ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
         "celeste_plan_destroy": (ctypes.c_int, [P]),
@@ -95,6 +98,7 @@ def lib():
 def exported_symbols():
     """Names the header declares, for the load check."""
     return ["celeste_create", "celeste_destroy", "celeste_synchronize", "celeste_launch_count",
+            "celeste_profile_enable", "celeste_profile_read",
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
             "celeste_elbo_grad_hess", "celeste_elbo", "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
@@ -144,13 +148,14 @@ def model_struct(model) -> _Model:
 
 
 class Context:
-    """A library context bound to a device and to torch's current stream."""
+    """A library context bound to a device and a stream (default: torch's
+    current stream)."""
 
-    def __init__(self, model, device: int = 0):
+    def __init__(self, model, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
         if not torch.cuda.is_available():
             raise CelesteError("no CUDA device: the library has no CPU path")
         self.device = torch.device("cuda", device)
-        self.stream = torch.cuda.current_stream(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._model = model_struct(model)
         h = ctypes.c_void_p()
         _check(lib().celeste_create(ctypes.byref(h), ctypes.byref(self._model), device,
@@ -165,6 +170,19 @@ class Context:
 
     def launches(self) -> int:
         return int(lib().celeste_launch_count(self.handle))
+
+    def profile(self, on: bool):
+        _check(lib().celeste_profile_enable(self.handle, 1 if on else 0), "celeste_profile_enable")
+
+    def profile_read(self, reset: bool = True):
+        """(kernel ms, timed launches, visits) of the derivative kernel."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        vis = ctypes.c_int64(0)
+        _check(lib().celeste_profile_read(self.handle, 1 if reset else 0, ctypes.byref(ms),
+                                          ctypes.byref(n), ctypes.byref(vis)),
+               "celeste_profile_read")
+        return ms.value, n.value, vis.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -21,6 +21,11 @@ struct celeste_ctx {
   unsigned int* d_err = nullptr;
   int n_exp = 0, n_dev = 0;
   int64_t launches = 0;
+  // event timing of the derivative pixel kernel (celeste_profile_*)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;   // start/stop pairs, reused
+  size_t n_timed = 0;                // pairs recorded since the last read
+  int64_t timed_visits = 0;
 };
 
 struct celeste_plan {
@@ -105,6 +110,28 @@ T* dev_alloc(celeste_plan* p, size_t count, int* err) {
   return static_cast<T*>(ptr);
 }
 
+// Launches the derivative pixel kernel, bracketed by events when profiling.
+cudaError_t derivs_launch(celeste_ctx* c, celeste_plan* p, const Launch& L) {
+  if (!c->profiling) return launch_pixels_derivs(L, p->v);
+  if (2 * (c->n_timed + 1) > c->events.size()) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      c->events.push_back(e);
+    }
+  }
+  cudaEvent_t e0 = c->events[2 * c->n_timed], e1 = c->events[2 * c->n_timed + 1];
+  cudaError_t r = cudaEventRecord(e0, L.stream);
+  if (r == cudaSuccess) r = launch_pixels_derivs(L, p->v);
+  if (r == cudaSuccess) r = cudaEventRecord(e1, L.stream);
+  if (r == cudaSuccess) {
+    ++c->n_timed;
+    c->timed_visits += p->visits;
+  }
+  return r;
+}
+
 int run_setup(celeste_ctx* c, celeste_plan* p, int first, int n, bool trial) {
   Launch L = make_launch(c, p);
   ++c->launches;
@@ -175,6 +202,7 @@ int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* 
 int celeste_destroy(celeste_ctx* c) {
   if (!c) return CELESTE_EINVAL;
   cudaSetDevice(c->device);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   cudaFree(c->d_model);
   cudaFree(c->d_err);
   delete c;
@@ -195,6 +223,34 @@ int celeste_synchronize(celeste_ctx* c, uint32_t* device_error) {
 }
 
 int64_t celeste_launch_count(const celeste_ctx* c) { return c ? c->launches : -1; }
+
+int celeste_profile_enable(celeste_ctx* c, int on) {
+  if (!c) return CELESTE_EINVAL;
+  c->profiling = on != 0;
+  c->n_timed = 0;
+  c->timed_visits = 0;
+  return CELESTE_OK;
+}
+
+int celeste_profile_read(celeste_ctx* c, int reset, double* total_ms, int64_t* launches,
+                         int64_t* visits) {
+  if (!c || !total_ms || !launches || !visits) return CELESTE_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  double ms = 0.0;
+  for (size_t k = 0; k < c->n_timed; ++k) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->events[2 * k], c->events[2 * k + 1]));
+    ms += t;
+  }
+  *total_ms = ms;
+  *launches = (int64_t)c->n_timed;
+  *visits = c->timed_visits;
+  if (reset) {
+    c->n_timed = 0;
+    c->timed_visits = 0;
+  }
+  return CELESTE_OK;
+}
 
 int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t* ids, int32_t n,
                         const celeste_tuning* tuning, celeste_plan** out) {
@@ -255,8 +311,8 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   // overlap an own patch
   std::unordered_map<int64_t, int> nb_index;
   for (int pp = 0; pp < n_own; ++pp) {
-    PairInfo& pi = pairs[pp];
-    pi.nbr_begin = (int)pair_nbr.size();
+    const PairInfo pi = pairs[pp];   // a copy: pairs grows inside the loop
+    pairs[pp].nbr_begin = (int)pair_nbr.size();
     const int s = pi.source;
     for (int k = pr->h_nbr_ptr[s]; k < pr->h_nbr_ptr[s + 1]; ++k) {
       const int t = pr->h_nbr_idx[k];
@@ -290,7 +346,6 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
           qn.nbr_begin = qn.nbr_end = 0;
           qn.item_begin = qn.item_end = 0;
           pairs.push_back(qn);
-          // pairs may have been reallocated
         } else {
           idx = it->second;
         }
@@ -379,7 +434,7 @@ static int eval_common(celeste_ctx* c, celeste_plan* p, bool derivs) {
   if (rc) return rc;
   c->launches += 2;
   CK(launch_background(L, p->v));
-  CK(derivs ? launch_pixels_derivs(L, p->v) : launch_pixels_value(L, p->v));
+  CK(derivs ? derivs_launch(c, p, L) : launch_pixels_value(L, p->v));
   return CELESTE_OK;
 }
 
@@ -417,7 +472,7 @@ int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, i
   if (rc) return rc;
   c->launches += 3;
   CK(launch_background(L, v));
-  CK(launch_pixels_derivs(L, v));
+  CK(derivs_launch(c, p, L));
   CK(launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess));
   if (elbo_rel) CK(cudaMemcpyAsync(elbo_rel, v.elbo_rel, v.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   c->launches += 1;
