@@ -45,6 +45,7 @@ extern "C" {
 #define CELESTE_EAGAIN      (-5)   /* serving: no capacity, retry later     */
 #define CELESTE_EBUSY       (-6)   /* serving: request not finished         */
 #define CELESTE_ENOTFOUND   (-7)   /* serving: unknown ticket               */
+#define CELESTE_ETOOLARGE   (-8)   /* request exceeds a fixed-size limit    */
 
 /* device error word bits (celeste_synchronize returns CELESTE_EDEVICE and
  * stores the word in *device_error when any is set) */
@@ -235,6 +236,41 @@ int celeste_render(celeste_ctx* ctx, const celeste_plan* plan, float* E_out, flo
 /* Sky plus the moments of the neighbours at each patch pixel of every
  * plan source (the background a source is fitted against). */
 int celeste_background(celeste_ctx* ctx, const celeste_plan* plan, float* bgE_out, float* bgV_out);
+
+/* Allocation-free evaluation, for callers that must not allocate device
+ * memory: code that runs while its memory pool is locked or being
+ * defragmented, plugins of a host program that owns every device
+ * allocation, and callers that cannot afford the synchronisation a
+ * cudaMalloc may bring mid-work.  (The paper has no counterpart: this is a
+ * property of the library, not of the method.)
+ *
+ * Computes what celeste_elbo_grad_hess computes (same kernels, same work
+ * decomposition) for the n sources h_src_ids (HOST array) of *problem, with
+ * no context and no plan: every intermediate lives in one file-scope device
+ * array of CELESTE_NOALLOC_BYTES that each GPU loading the library holds
+ * until the process exits.  It calls no cudaMalloc/cudaFree and no
+ * allocating routine; model constants and the work decomposition are staged
+ * from static host arrays with cudaMemcpyAsync.  Runs on the current device
+ * and on cuda_stream (a cudaStream_t, or NULL).  Outputs as in
+ * celeste_elbo_grad_hess; device_error (device uint32, may be NULL)
+ * receives the device error word of this call.
+ *
+ * The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Limits: at most CELESTE_NOALLOC_MAX_SOURCES
+ * sources, 4096 (source, image) patches including neighbours' patches,
+ * 32768 pixel tiles of 256 pixels, and everything within the byte size;
+ * larger requests return CELESTE_ETOOLARGE before any work is queued.
+ * Every call shares the array and finds the previous call's contents in
+ * it (what must start at zero is cleared each call): calls that overlap on
+ * the GPU (on different streams, or from several host threads) race, so
+ * serialise them. */
+#define CELESTE_NOALLOC_BYTES        (16u << 20)
+#define CELESTE_NOALLOC_MAX_SOURCES  1024
+int celeste_elbo_grad_hess_noalloc(const celeste_model* model, const celeste_problem* problem,
+                                   const int32_t* h_src_ids, int32_t n, void* cuda_stream,
+                                   double* elbo, double* elbo_rel, double* grad, double* hess,
+                                   uint32_t* device_error);
 
 /* Greedy colouring of the overlap graph by ascending source id (host):
  * colour[s] = smallest colour unused by lower-id neighbours.  Returns the

@@ -86,6 +86,9 @@ def lib():
         "celeste_render": (ctypes.c_int, [P, P, P, P]),
         "celeste_background": (ctypes.c_int, [P, P, P, P]),
         "celeste_color_sources": (ctypes.c_int, [I32, P, P, P]),
+        "celeste_elbo_grad_hess_noalloc": (ctypes.c_int, [ctypes.POINTER(_Model),
+                                                          ctypes.POINTER(_Problem), P, I32, P,
+                                                          P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -102,7 +105,7 @@ def exported_symbols():
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
             "celeste_elbo_grad_hess", "celeste_elbo", "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
-            "celeste_color_sources"]
+            "celeste_color_sources", "celeste_elbo_grad_hess_noalloc"]
 
 
 class CelesteError(RuntimeError):
@@ -378,3 +381,20 @@ def color_sources(nbr_ptr: np.ndarray, nbr_idx: np.ndarray) -> np.ndarray:
 def color_classes(problem) -> list:
     col = color_sources(problem.nbr_ptr, problem.nbr_idx)
     return [np.flatnonzero(col == c).astype(np.int32) for c in range(int(col.max()) + 1 if len(col) else 0)]
+
+
+def elbo_grad_hess_noalloc(model, dprob: DeviceProblem, sources: Sequence[int], out,
+                           stream: Optional[torch.cuda.Stream] = None,
+                           device_error: Optional[torch.Tensor] = None):
+    """The allocation-free entry point: fills ``out`` = (elbo, elbo_rel, grad,
+    hess), caller-allocated device tensors, on ``stream`` (torch's current
+    stream by default).  For callers that must not allocate device memory;
+    see the header for its limits and its shared scratch array."""
+    ids = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    m = model_struct(model)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    e, er, g, H = out
+    return _check(lib().celeste_elbo_grad_hess_noalloc(
+        ctypes.byref(m), ctypes.byref(dprob.struct), ids.ctypes.data if ids.size else None,
+        int(ids.size), ctypes.c_void_p(st.cuda_stream), _ptr(e), _ptr(er), _ptr(g), _ptr(H),
+        _ptr(device_error)), "celeste_elbo_grad_hess_noalloc")
