@@ -37,44 +37,107 @@ struct TrSmem {
   double z[32];
   double w[32];
   double red[32];
+  float df[32], ef[32], e2f[32], gf[32];   // T and Q^T g scaled by 1 / scale, FP32
 };
 
-// Number of negative pivots of T - sigma I (Sturm count).
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, double sigma) {
+// Sturm count of T - sigma I in FP32 (pivot recurrence; scaled T, |T| <= 1).
+__device__ __forceinline__ int sturm32(const float* d, const float* e2, float sigma) {
   int cnt = 0;
-  double q = d[0] - sigma;
-  if (q < 0.0) ++cnt;
+  float q = d[0] - sigma;
+  cnt += q < 0.f;
 #pragma unroll 1
   for (int i = 1; i < N; ++i) {
-    double qp = q == 0.0 ? 1e-300 : q;
-    q = (d[i] - sigma) - e[i - 1] * e[i - 1] / qp;
-    if (q < 0.0) ++cnt;
+    const float qp = q == 0.f ? 1e-30f : q;
+    q = (d[i] - sigma) - __fdividef(e2[i - 1], qp);
+    cnt += q < 0.f;
   }
   return cnt;
 }
 
-// Solves (T + lam I) y = rhs (T + lam I positive definite), returns |y|^2
-// and writes y when out != nullptr.
-__device__ __noinline__ double tri_solve(const double* d, const double* e, const double* rhs,
-                                         double lam, double* out) {
-  double cp[N], gp[N];
-  double m = d[0] + lam;
-  cp[0] = e[0] / m;
-  gp[0] = rhs[0] / m;
+// Sturm count of T - sigma I in FP64 without divisions: sign changes of the
+// characteristic-polynomial sequence p_0 = 1, p_1 = d_0 - sigma,
+// p_{i+1} = (d_i - sigma) p_i - e_{i-1}^2 p_{i-1} (scaled T keeps |p_i| <= 3^27).
+__device__ __forceinline__ int sturm64(const double* d, const double* e, double sigma) {
+  double pm = 1.0, p = d[0] - sigma;
+  int cnt = (p < 0.0);
+  bool neg = p < 0.0 || (p == 0.0);
+#pragma unroll 1
+  for (int i = 1; i < N; ++i) {
+    const double pn = (d[i] - sigma) * p - e[i - 1] * e[i - 1] * pm;
+    const bool nn = pn < 0.0 || (pn == 0.0 && !neg);
+    cnt += (nn != neg);
+    neg = nn;
+    pm = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+// |y|^2 for (T + lam I) y = g in FP32 (scaled problem).
+__device__ __noinline__ float norm2_32(const float* d, const float* e, const float* g, float lam) {
+  float cp[N], gp[N];
+  float m = d[0] + lam;
+  float r = __frcp_rn(m);
+  cp[0] = e[0] * r;
+  gp[0] = g[0] * r;
 #pragma unroll
   for (int i = 1; i < N; ++i) {
     m = (d[i] + lam) - e[i - 1] * cp[i - 1];
-    cp[i] = i < N - 1 ? e[i] / m : 0.0;
-    gp[i] = (rhs[i] - e[i - 1] * gp[i - 1]) / m;
+    r = __frcp_rn(m);
+    cp[i] = i < N - 1 ? e[i] * r : 0.f;
+    gp[i] = (g[i] - e[i - 1] * gp[i - 1]) * r;
   }
-  double y = gp[N - 1];
-  double s = y * y;
-  if (out) out[N - 1] = y;
+  float y = gp[N - 1], s = y * y;
 #pragma unroll
   for (int i = N - 2; i >= 0; --i) {
     y = gp[i] - cp[i] * y;
     s += y * y;
-    if (out) out[i] = y;
+  }
+  return s;
+}
+
+// LDL^T of T + lam I (positive definite) and y = (T + lam I)^{-1} rhs.
+// Returns |y|^2; q = y^T (T + lam I)^{-1} y (for the Newton step on the
+// secular equation); writes y when out != nullptr.  One division per row.
+__device__ __noinline__ double ldl_solve(const double* d, const double* e, const double* rhs, double lam,
+                            double* out, double* q) {
+  double l[N], rD[N], w[N];
+  double D = d[0] + lam;
+  rD[0] = 1.0 / D;
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    l[i - 1] = e[i - 1] * rD[i - 1];
+    D = (d[i] + lam) - l[i - 1] * e[i - 1];
+    rD[i] = 1.0 / D;
+  }
+  double z = rhs[0];
+  w[0] = z * rD[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    z = rhs[i] - l[i - 1] * z;
+    w[i] = z * rD[i];
+  }
+  double y = w[N - 1], s = y * y;
+  double ys[N];
+  ys[N - 1] = y;
+#pragma unroll
+  for (int i = N - 2; i >= 0; --i) {
+    y = w[i] - l[i] * y;
+    ys[i] = y;
+    s += y * y;
+  }
+  if (out) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = ys[i];
+  }
+  if (q) {
+    double u = ys[0], acc = u * u * rD[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+      u = ys[i] - l[i - 1] * u;
+      acc += u * u * rD[i];
+    }
+    *q = acc;
   }
   return s;
 }
@@ -158,21 +221,51 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   const double* d = S.d;
   const double* e = S.e;
   const double* gh = S.gh;
-  double gn2 = 0.0, scale = 0.0, a = 1e300, b = -1e300;
+  double gn2 = 0.0, scale = 0.0;
   for (int i = 0; i < N; ++i) {
-    const double r = fabs(e[i]) + (i ? fabs(e[i - 1]) : 0.0);
     gn2 += gh[i] * gh[i];
-    scale = fmax(scale, fabs(d[i]) + r);
-    a = fmin(a, d[i] - r);
-    b = fmax(b, d[i] + r);
+    scale = fmax(scale, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : 0.0));
   }
   scale = fmax(scale, 1e-300);
-  // ---- lambda_min(T) by multisection on Sturm counts (Gershgorin bracket)
-  a -= 1e-12 * scale;
-  b += 1e-12 * scale;
-  for (int round = 0; round < 14; ++round) {
+  const double inv = 1.0 / scale;
+  // scaled copies: |T / scale| <= 1
+  if (lane < N) {
+    S.df[lane] = (float)(d[lane] * inv);
+    S.ef[lane] = (float)(e[lane] * inv);
+    S.e2f[lane] = S.ef[lane] * S.ef[lane];
+    S.w[lane] = e[lane] * inv;      // FP64 scaled off-diagonal
+    S.z[lane] = d[lane] * inv;      // FP64 scaled diagonal
+  }
+  __syncwarp();
+  // ---- lambda_min(T): FP32 multisection on the scaled matrix, then FP64
+  // multisection with the division-free Sturm sequence
+  double a = 1.0, b = -1.0;
+  for (int i = 0; i < N; ++i) {
+    const double r = fabs(S.w[i]) + (i ? fabs(S.w[i - 1]) : 0.0);
+    a = fmin(a, S.z[i] - r);
+    b = fmax(b, S.z[i] + r);
+  }
+  a -= 1e-6;
+  b += 1e-6;
+  {
+    float fa = (float)a, fb = (float)b;
+    for (int round = 0; round < 5; ++round) {
+      const float sig = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
+      const bool hit = lane < 31 && sturm32(S.df, S.e2f, sig) >= 1;
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      const int t = mask ? __ffs(mask) - 1 : 31;
+      const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
+      const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
+      fa = na;
+      fb = nb;
+    }
+    // FP32 counts are exact away from eigenvalues to ~1e-6 of the scale
+    a = fmax(a, (double)fa - 1e-5);
+    b = fmin(b, (double)fb + 1e-5);
+  }
+  for (int round = 0; round < 5; ++round) {
     const double sig = a + (b - a) * (double)(lane + 1) / 32.0;
-    const bool hit = lane < 31 && sturm_count(d, e, sig) >= 1;
+    const bool hit = lane < 31 && sturm64(S.z, S.w, sig) >= 1;
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int t = mask ? __ffs(mask) - 1 : 31;
     const double na = t == 0 ? a : a + (b - a) * (double)t / 32.0;
@@ -180,35 +273,54 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     a = na;
     b = nb;
   }
-  const double lmin = 0.5 * (a + b);
+  const double lmin = 0.5 * (a + b) * scale;
   // ---- multiplier
   const double D2 = Delta * Delta;
   double lam = 0.0;
   bool interior = false, hard = false;
-  if (lmin > 0.0) interior = tri_solve(d, e, gh, 0.0, nullptr) <= D2;
+  if (lmin > 0.0) interior = ldl_solve(d, e, gh, 0.0, nullptr, nullptr) <= D2;
   if (!interior) {
     const double lo = fmax(0.0, -lmin);
     const double eps = 1e-12 * scale;
     double la = lo + eps;
     double lb = lo + sqrt(gn2) / Delta + eps;
-    if (tri_solve(d, e, gh, la, nullptr) <= D2) {
+    if (ldl_solve(d, e, gh, la, nullptr, nullptr) <= D2) {
       hard = true;
       lam = la;
     } else {
-      for (int round = 0; round < 16; ++round) {
-        const double l = la + (lb - la) * (double)(lane + 1) / 32.0;
-        const bool inside = lane < 31 && tri_solve(d, e, gh, l, nullptr) <= D2;
+      // FP32 multisection on the scaled problem for a starting point ...
+      if (lane < N) S.gf[lane] = (float)(gh[lane] * inv);
+      __syncwarp();
+      const float D2s = (float)(D2);          // |y| is scale-invariant
+      float fa = (float)(la * inv), fb = (float)(lb * inv);
+      for (int round = 0; round < 6; ++round) {
+        const float l = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
+        const bool inside = lane < 31 && norm2_32(S.df, S.ef, S.gf, l) <= D2s;
         const unsigned mask = __ballot_sync(0xffffffffu, inside);
         const int t = mask ? __ffs(mask) - 1 : 31;
-        const double na = t == 0 ? la : la + (lb - la) * (double)t / 32.0;
-        const double nb = t == 31 ? lb : la + (lb - la) * (double)(t + 1) / 32.0;
-        la = na;
-        lb = nb;
+        const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
+        const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
+        fa = na;
+        fb = nb;
       }
-      lam = lb;
+      // ... then safeguarded Newton on 1/|y(l)| - 1/Delta in FP64
+      // (Nocedal & Wright, Algorithm 4.3), kept inside [la, lb]
+      double l = fmin(fmax((double)fb * scale, la), lb);
+      for (int it = 0; it < 12; ++it) {
+        double q;
+        const double n2 = ldl_solve(d, e, gh, l, nullptr, &q);
+        const double ny = sqrt(n2);
+        if (n2 <= D2) lb = l; else la = l;
+        lam = l;
+        if (fabs(ny - Delta) <= 1e-13 * Delta) break;
+        double ln = l + (ny - Delta) / Delta * n2 / q;
+        if (!(ln > la && ln < lb)) ln = 0.5 * (la + lb);
+        if (ln == l) break;
+        l = ln;
+      }
     }
   }
-  if (lane == 0) tri_solve(d, e, gh, lam, S.y);
+  if (lane == 0) ldl_solve(d, e, gh, lam, S.y, nullptr);
   __syncwarp();
   if (hard) {
     // eigenvector of lambda_min by inverse iteration, shifted just below it
@@ -216,9 +328,9 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
       const double shift = -lmin + 1e-10 * scale;
       for (int i = 0; i < N; ++i) S.w[i] = 1.0 / sqrt((double)N);
       for (int itn = 0; itn < 4; ++itn) {
-        const double nz = tri_solve(d, e, S.w, shift, S.z);
-        const double inv = 1.0 / sqrt(nz);
-        for (int i = 0; i < N; ++i) S.w[i] = S.z[i] * inv;
+        const double nz = ldl_solve(d, e, S.w, shift, S.z, nullptr);
+        const double r = 1.0 / sqrt(nz);
+        for (int i = 0; i < N; ++i) S.w[i] = S.z[i] * r;
       }
       // project z out of y
       double zy = 0.0;
