@@ -145,45 +145,64 @@ int run_setup(celeste_ctx* c, celeste_plan* p, int first, int n, bool trial) {
 
 }  // namespace
 
+namespace celeste {
+
+bool prepare_model(const celeste_model* m, ModelDev* md) {
+  if (m->n_exp < 1 || m->n_exp > kMaxProf || m->n_dev < 1 || m->n_dev > kMaxProf ||
+      m->n_color < 1 || m->n_color > kMaxColor || !(m->prior_a > 0.0 && m->prior_a < 1.0) ||
+      !(m->e_radius[1] > 0.0))
+    return false;
+  memset(md, 0, sizeof(*md));
+  md->n_exp = m->n_exp;
+  md->n_dev = m->n_dev;
+  md->n_color = m->n_color;
+  for (int j = 0; j < kMaxProf; ++j) {
+    md->alpha_exp[j] = m->alpha_exp[j];
+    md->tau_exp[j] = m->tau_exp[j];
+    md->alpha_dev[j] = m->alpha_dev[j];
+    md->tau_dev[j] = m->tau_dev[j];
+  }
+  md->prior_a = m->prior_a;
+  for (int i = 0; i < 2; ++i) {
+    if (!(m->prior_r[i][1] > 0.0)) return false;
+    md->prior_r[i][0] = m->prior_r[i][0];
+    md->prior_r[i][1] = m->prior_r[i][1];
+    md->log_prior_r2[i] = log(m->prior_r[i][1]);
+    for (int j = 0; j < m->n_color; ++j) {
+      if (!(m->color_w[i][j] > 0.0)) return false;
+      md->color_w[i][j] = m->color_w[i][j];
+      md->log_color_w[i][j] = log(m->color_w[i][j]);
+      for (int k = 0; k < 4; ++k) md->color_mean[i][j][k] = m->color_mean[i][j][k];
+      if (!spd_inverse4(m->color_cov[i][j], md->color_prec[i][j], &md->color_logdet[i][j]))
+        return false;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    md->e_radius[k] = m->e_radius[k];
+    md->e_profile[k] = m->e_profile[k];
+    md->e_axis[k] = m->e_axis[k];
+  }
+  if (!(m->e_axis[0] > 0.0 && m->e_axis[1] > 0.0 && m->e_profile[0] > 0.0 && m->e_profile[1] > 0.0))
+    return false;
+  md->log_prior_a = log(m->prior_a);
+  md->log1m_prior_a = log1p(-m->prior_a);
+  md->logit_prior_a = md->log_prior_a - md->log1m_prior_a;
+  md->half_log_2pi_e2 = 0.5 * log(2.0 * M_PI * m->e_radius[1]);
+  md->log_beta_axis = lgamma(m->e_axis[0]) + lgamma(m->e_axis[1]) - lgamma(m->e_axis[0] + m->e_axis[1]);
+  md->log_beta_profile =
+      lgamma(m->e_profile[0]) + lgamma(m->e_profile[1]) - lgamma(m->e_profile[0] + m->e_profile[1]);
+  return true;
+}
+
+}  // namespace celeste
+
 extern "C" {
 
 int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* stream) {
   if (!out || !m) return CELESTE_EINVAL;
   *out = nullptr;
-  if (m->n_exp < 1 || m->n_exp > kMaxProf || m->n_dev < 1 || m->n_dev > kMaxProf ||
-      m->n_color < 1 || m->n_color > kMaxColor)
-    return CELESTE_EINVAL;
-  if (!(m->prior_a > 0.0 && m->prior_a < 1.0)) return CELESTE_EINVAL;
   ModelDev md;
-  memset(&md, 0, sizeof(md));
-  md.n_exp = m->n_exp;
-  md.n_dev = m->n_dev;
-  md.n_color = m->n_color;
-  for (int j = 0; j < kMaxProf; ++j) {
-    md.alpha_exp[j] = m->alpha_exp[j];
-    md.tau_exp[j] = m->tau_exp[j];
-    md.alpha_dev[j] = m->alpha_dev[j];
-    md.tau_dev[j] = m->tau_dev[j];
-  }
-  md.prior_a = m->prior_a;
-  for (int i = 0; i < 2; ++i) {
-    if (!(m->prior_r[i][1] > 0.0)) return CELESTE_EINVAL;
-    md.prior_r[i][0] = m->prior_r[i][0];
-    md.prior_r[i][1] = m->prior_r[i][1];
-    for (int j = 0; j < m->n_color; ++j) {
-      if (!(m->color_w[i][j] > 0.0)) return CELESTE_EINVAL;
-      md.color_w[i][j] = m->color_w[i][j];
-      for (int k = 0; k < 4; ++k) md.color_mean[i][j][k] = m->color_mean[i][j][k];
-      if (!spd_inverse4(m->color_cov[i][j], md.color_prec[i][j], &md.color_logdet[i][j]))
-        return CELESTE_EINVAL;
-    }
-  }
-  for (int k = 0; k < 2; ++k) {
-    md.e_radius[k] = m->e_radius[k];
-    md.e_profile[k] = m->e_profile[k];
-    md.e_axis[k] = m->e_axis[k];
-  }
-  if (!(md.e_radius[1] > 0.0)) return CELESTE_EINVAL;
+  if (!prepare_model(m, &md)) return CELESTE_EINVAL;
   CK(cudaSetDevice(device));
   celeste_ctx* c = new celeste_ctx();
   c->device = device;

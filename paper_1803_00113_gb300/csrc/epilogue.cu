@@ -33,13 +33,18 @@ constexpr int kNu = 26;   // 20 flux moments (band b, kind e at 4b+e), u (2), Si
 constexpr int kNuPad = 32;
 constexpr int kKlVals = 8 + 36 + 10 + 4;   // per colour component: grad, outer, prec, diag
 
+// Transcendentals of single parameters run in FP32 (relative error ~1e-7,
+// far inside the tolerances); the arithmetic that combines them stays FP64.
 __device__ __forceinline__ double sigm(double t) {
-  return t >= 0.0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
+  const float f = (float)t;
+  return (double)(f >= 0.f ? 1.f / (1.f + expf(-f)) : expf(f) / (1.f + expf(f)));
 }
 // log(1 + exp(t)) without overflow
 __device__ __forceinline__ double softplus(double t) {
-  return t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
+  const float f = (float)t;
+  return (double)(f > 0.f ? f + log1pf(expf(-f)) : log1pf(expf(f)));
 }
+__device__ __forceinline__ double exp1(double t) { return (double)expf((float)t); }
 
 struct EpiSmem {
   double W[kAcc];                  // one pair's sums
@@ -89,34 +94,36 @@ __device__ double kappa_logderivs(const double* th, int a, double* dl, double* d
   dl[0] = i ? q0 : -q1;
   d2l[0] = -q0 * q1;
   const int ir = 1 + 2 * i, iv = 2 + 2 * i;
-  double m = th[ir], v = exp(th[iv]);
+  double m = th[ir], v = exp1(th[iv]);
   dl[ir] = am;
   dl[iv] = av * v;
   d2l[iv] = dl[iv];
   for (int k = 0; k < 4; ++k) {
     const double s = (double)kSelE[b][k];
-    const double cvk = exp(th[13 + 4 * i + k]);
+    const double cvk = exp1(th[13 + 4 * i + k]);
     m += s * th[5 + 4 * i + k];
     v += s * s * cvk;
     dl[5 + 4 * i + k] = am * s;
     dl[13 + 4 * i + k] = av * s * s * cvk;
     d2l[13 + 4 * i + k] = dl[13 + 4 * i + k];
   }
-  return exp(logq + am * m + av * v);
+  return exp1(logq + am * m + av * v);
 }
 
 // Derivatives of Sigma_s = (S11, S12, S22) over (angle, log radius, logit axis).
 __device__ void sigma_derivs(const double* th, double dS[3][3], double d2S[3][3][3]) {
   const double phi = th[23], lr = th[24];
   const double ax = sigm(th[25]);
-  const double e2 = exp(2.0 * lr);
+  const double e2 = exp1(2.0 * lr);
   const double a2 = ax * ax;
   const double a2t = 2.0 * a2 * (1.0 - ax);
   const double a2tt = 2.0 * a2 * (1.0 - ax) * (2.0 - 3.0 * ax);
   const double P = 0.5 * e2 * (1.0 + a2), Qd = 0.5 * e2 * (1.0 - a2);
   const double Pl = 2.0 * P, Pll = 4.0 * P, Pt = 0.5 * e2 * a2t, Ptt = 0.5 * e2 * a2tt, Plt = 2.0 * Pt;
   const double Ql = 2.0 * Qd, Qll = 4.0 * Qd, Qt = -0.5 * e2 * a2t, Qtt = -0.5 * e2 * a2tt, Qlt = 2.0 * Qt;
-  const double C2 = cos(2.0 * phi), S2 = sin(2.0 * phi);
+  float s2f, c2f;
+  sincosf((float)(2.0 * phi), &s2f, &c2f);
+  const double C2 = c2f, S2 = s2f;
   // S11 = P + Qd C2, S22 = P - Qd C2, S12 = -Qd S2
   for (int e = 0; e < 3; e += 2) {
     const double s = e == 0 ? 1.0 : -1.0;
@@ -159,7 +166,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
       double tr = 0.0, quad = 0.0, slv = 0.0;
       for (int k = 0; k < 4; ++k) {
         d[k] = cm[k] - m->color_mean[i][j][k];
-        cv[k] = exp(lcv[k]);
+        cv[k] = exp1(lcv[k]);
       }
       for (int k = 0; k < 4; ++k) {
         double s = 0.0;
@@ -170,7 +177,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
         slv += lcv[k];
       }
       const double K = 0.5 * (tr + quad - 4.0 + m->color_logdet[i][j] - slv);
-      S.klj[lane] = log(m->color_w[i][j]) - K;
+      S.klj[lane] = m->log_color_w[i][j] - K;
       if (kDerivs) {
         double* o = S.klc + lane * kKlVals;
         double gk[8];
@@ -196,7 +203,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
     const int i = lane / kMaxColor;
     double mx = -INFINITY;
     for (int j = 0; j < J; ++j) mx = fmax(mx, S.klj[i * kMaxColor + j]);
-    S.kw[lane] = (lane % kMaxColor) < J ? exp(S.klj[lane] - mx) : 0.0;   // scratch
+    S.kw[lane] = (lane % kMaxColor) < J ? exp1(S.klj[lane] - mx) : 0.0;   // scratch
     S.kls[4 + i] = mx;
   }
   __syncwarp();
@@ -204,7 +211,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   for (int i = 0; i < 2; ++i) {
     se[i] = 0.0;
     for (int j = 0; j < J; ++j) se[i] += S.kw[i * kMaxColor + j];
-    Bval[i] = -(S.kls[4 + i] + log(se[i]));
+    Bval[i] = -(S.kls[4 + i] + (double)logf((float)se[i]));
   }
   if (kDerivs) {
     // pi-weighted sums of the per-component pieces, per type (lanes over values)
@@ -218,24 +225,23 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   }
   __syncwarp();
   // ---- assemble (lane 0 for the value, lanes over entries for the derivatives)
-  const double pa = m->prior_a;
   if (lane == 0) {
-    double v = a * (-softplus(-th[0]) - log(pa)) + (1.0 - a) * (-softplus(th[0]) - log1p(-pa));
+    double v = a * (-softplus(-th[0]) - m->log_prior_a) + (1.0 - a) * (-softplus(th[0]) - m->log1m_prior_a);
     for (int i = 0; i < 2; ++i) {
       const double R1 = m->prior_r[i][0], R2 = m->prior_r[i][1];
-      const double rm = th[1 + 2 * i], lrv = th[2 + 2 * i], rv = exp(lrv);
-      const double klr = 0.5 * (log(R2) - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.0);
+      const double rm = th[1 + 2 * i], lrv = th[2 + 2 * i], rv = exp1(lrv);
+      const double klr = 0.5 * (m->log_prior_r2[i] - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.0);
       S.kls[2 + i] = klr + Bval[i];
       v += (i ? a : 1.0 - a) * S.kls[2 + i];
     }
     const double lr = th[24], E1 = m->e_radius[0], E2 = m->e_radius[1];
-    v += lr + 0.5 * log(2.0 * M_PI * E2) + (lr - E1) * (lr - E1) / (2.0 * E2);
+    v += lr + m->half_log_2pi_e2 + (lr - E1) * (lr - E1) / (2.0 * E2);
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
       const double b1 = which ? m->e_profile[0] : m->e_axis[0];
       const double b2 = which ? m->e_profile[1] : m->e_axis[1];
-      v += (b1 - 1.0) * softplus(-th[t]) + (b2 - 1.0) * softplus(th[t]) + lgamma(b1) +
-           lgamma(b2) - lgamma(b1 + b2);
+      v += (b1 - 1.0) * softplus(-th[t]) + (b2 - 1.0) * softplus(th[t]) +
+           (which ? m->log_beta_profile : m->log_beta_axis);
     }
     S.kls[0] = v;
   }
@@ -250,7 +256,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
     const int i = e / 100, k = (e % 100) / 10, l = e % 10;
     const double* pw = S.X + i * 64;            // pi-weighted: grad(8), outer(36), prec(10), diag(4)
     const double R2 = m->prior_r[i][1];
-    const double rm = th[1 + 2 * i], rv = exp(th[2 + 2 * i]);
+    const double rm = th[1 + 2 * i], rv = exp1(th[2 + 2 * i]);
     // gradient of K_i = KL_r + B at local k
     auto gK = [&](int kk) {
       if (kk == 0) return (rm - m->prior_r[i][0]) / R2;
@@ -286,7 +292,7 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   }
   __syncwarp();
   if (lane == 0) {
-    const double la = log(pa) - log1p(-pa);
+    const double la = m->logit_prior_a;
     const double d2q = wq * (1.0 - 2.0 * a);
     S.gth[0] -= wq * (th[0] - la) + wq * (S.kls[3] - S.kls[2]);
     S.Hth[0] -= wq * ((1.0 - 2.0 * a) * (th[0] - la) + 1.0) + d2q * (S.kls[3] - S.kls[2]);

@@ -74,7 +74,17 @@ struct ModelDev {
   double color_prec[2][kMaxColor][4][4];   // inverse covariances
   double color_logdet[2][kMaxColor];
   double e_radius[2], e_profile[2], e_axis[2];
+  // constants of the KL terms, precomputed on the host
+  double log_color_w[2][kMaxColor];
+  double log_prior_a, log1m_prior_a, logit_prior_a;
+  double log_prior_r2[2];
+  double half_log_2pi_e2;          // 0.5 log(2 pi E_radius,2)
+  double log_beta_axis, log_beta_profile;
 };
+
+// Validates *m and fills *md (colour precisions, log-determinants and the KL
+// constants).  Returns false for an invalid model.
+bool prepare_model(const celeste_model* m, ModelDev* md);
 
 // Everything a kernel needs about a plan, by value.
 struct PlanView {

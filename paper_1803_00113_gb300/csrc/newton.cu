@@ -1,16 +1,23 @@
 // FP64 trust-region Newton step (Sec. 4.3): maximise g.p + p.H.p / 2 over
 // the ball |p| <= Delta exactly, then accept or reject the trial point.
 //
-// GB300 has little FP64 throughput, so the 27 x 27 subproblem avoids a full
-// eigendecomposition: B = -H is reduced to tridiagonal form T = Q^T B Q by
-// Householder reflections (one warp, lanes over rows), and everything after
-// that is O(n) per evaluation on T:
-//   * lambda_min(T) by multisection on Sturm counts (31 probes per round);
-//   * the multiplier l solving |(T + l I)^{-1} Q^T g| = Delta by multisection
-//     on the (monotone) step norm, each lane running one tridiagonal solve;
+// GB300 issues a warp-wide FP64 instruction about every 64 cycles per SM
+// sub-partition, so the cost of this kernel is its count of FP64 warp
+// instructions, and a source gets four warps (one per sub-partition) for
+// the part that parallelises:
+//   * B = -H is reduced to tridiagonal form T = Q^T B Q by Householder
+//     reflections; rows are spread over the lanes and columns over the four
+//     warps;
+//   * lambda_min(T): multisection on Sturm counts, first in FP32 on the
+//     scaled matrix, then refined in FP64 with the division-free
+//     characteristic-polynomial sequence (31 probes per round);
+//   * the multiplier l solving |(T + l I)^{-1} Q^T g| = Delta: FP32
+//     multisection for a starting point, then the safeguarded Newton
+//     iteration on 1/|y(l)| - 1/Delta (Nocedal & Wright, Algorithm 4.3),
+//     each FP64 evaluation one LDL^T factorisation of T + l I;
 //   * the hard case (g orthogonal to the eigenvector of lambda_min) adds
-//     that eigenvector, found by inverse iteration, to reach the boundary;
-//     its sign makes the first nonzero entry of Q z positive;
+//     that eigenvector, from inverse iteration, to reach the boundary; its
+//     sign makes the first nonzero entry of Q z positive;
 //   * p = Q y and the predicted gain g.p + p.H.p/2 = y.Q^T g - y.T.y/2.
 // Trust-region constants follow the textbook loop (Nocedal & Wright,
 // Algorithm 4.1): accept when rho > 0.1, shrink to |p|/4 when rho < 1/4,
@@ -22,6 +29,7 @@
 namespace celeste {
 
 constexpr int N = kTheta;
+constexpr int kTrThreads = 128;
 constexpr double kEta = 0.1;
 constexpr double kDeltaMax = 100.0;
 constexpr double kFtol = 1e-9;
@@ -29,16 +37,28 @@ constexpr double kDeltaMin = 1e-8;
 
 struct TrSmem {
   double B[N * N];
-  double beta[N];
+  double beta[32];
   double gh[32];
   double d[32];
   double e[32];
+  double ds[32], es[32], gs[32];   // scaled T and Q^T g (|T / scale| <= 1)
   double y[32];
   double z[32];
   double w[32];
-  double red[32];
-  float df[32], ef[32], e2f[32], gf[32];   // T and Q^T g scaled by 1 / scale, FP32
+  double part[4 * 32];
+  double red[8];
+  float df[32], ef[32], e2f[32], gf[32];
+  int skip[32];                    // per Householder step: column already reduced
 };
+
+// 1 / x in FP64 from an FP32 seed and two Newton steps (|x| within FP32
+// range; callers pass scaled values).
+__device__ __forceinline__ double rcp64(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
 
 // Sturm count of T - sigma I in FP32 (pivot recurrence; scaled T, |T| <= 1).
 __device__ __forceinline__ int sturm32(const float* d, const float* e2, float sigma) {
@@ -60,7 +80,7 @@ __device__ __forceinline__ int sturm32(const float* d, const float* e2, float si
 __device__ __forceinline__ int sturm64(const double* d, const double* e, double sigma) {
   double pm = 1.0, p = d[0] - sigma;
   int cnt = (p < 0.0);
-  bool neg = p < 0.0 || (p == 0.0);
+  bool neg = p <= 0.0;
 #pragma unroll 1
   for (int i = 1; i < N; ++i) {
     const double pn = (d[i] - sigma) * p - e[i - 1] * e[i - 1] * pm;
@@ -96,53 +116,45 @@ __device__ __noinline__ float norm2_32(const float* d, const float* e, const flo
   return s;
 }
 
-// LDL^T of T + lam I (positive definite) and y = (T + lam I)^{-1} rhs.
-// Returns |y|^2; q = y^T (T + lam I)^{-1} y (for the Newton step on the
-// secular equation); writes y when out != nullptr.  One division per row.
-__device__ __noinline__ double ldl_solve(const double* d, const double* e, const double* rhs, double lam,
-                            double* out, double* q) {
+// LDL^T of T + lam I (positive definite; scaled T) and y = (T + lam I)^{-1} rhs.
+// Returns |y|^2; q = y^T (T + lam I)^{-1} y when q != nullptr; y into out.
+__device__ __noinline__ double ldl_solve(const double* d, const double* e, const double* rhs,
+                                         double lam, double* out, double* q) {
   double l[N], rD[N], w[N];
-  double D = d[0] + lam;
-  rD[0] = 1.0 / D;
+  rD[0] = rcp64(d[0] + lam);
 #pragma unroll
   for (int i = 1; i < N; ++i) {
     l[i - 1] = e[i - 1] * rD[i - 1];
-    D = (d[i] + lam) - l[i - 1] * e[i - 1];
-    rD[i] = 1.0 / D;
+    rD[i] = rcp64((d[i] + lam) - l[i - 1] * e[i - 1]);
   }
   double z = rhs[0];
   w[0] = z * rD[0];
 #pragma unroll
   for (int i = 1; i < N; ++i) {
-    z = rhs[i] - l[i - 1] * z;
+    z = fma(-l[i - 1], z, rhs[i]);
     w[i] = z * rD[i];
   }
   double y = w[N - 1], s = y * y;
-  double ys[N];
-  ys[N - 1] = y;
+  out[N - 1] = y;
 #pragma unroll
   for (int i = N - 2; i >= 0; --i) {
-    y = w[i] - l[i] * y;
-    ys[i] = y;
-    s += y * y;
-  }
-  if (out) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) out[i] = ys[i];
+    y = fma(-l[i], y, w[i]);
+    out[i] = y;
+    s = fma(y, y, s);
   }
   if (q) {
-    double u = ys[0], acc = u * u * rD[0];
+    double u = out[0], acc = u * u * rD[0];
 #pragma unroll
     for (int i = 1; i < N; ++i) {
-      u = ys[i] - l[i - 1] * u;
-      acc += u * u * rD[i];
+      u = fma(-l[i - 1], u, out[i]);
+      acc = fma(u * u, rD[i], acc);
     }
     *q = acc;
   }
   return s;
 }
 
-// Applies the reflections: forward (Q^T x: H_0 first) or backward (Q x).
+// Applies the reflections (warp 0): Q^T x (H_0 first) or Q x (H_0 last).
 __device__ void apply_q(TrSmem& S, double* x, bool transpose, int lane) {
   for (int step = 0; step < N - 2; ++step) {
     const int k = transpose ? step : N - 3 - step;
@@ -152,64 +164,89 @@ __device__ void apply_q(TrSmem& S, double* x, bool transpose, int lane) {
     const double vi = lane < m ? S.B[(k + 1 + lane) * N + k] : 0.0;
     const double xi = lane < m ? x[k + 1 + lane] : 0.0;
     const double s = warp_sum_d(vi * xi);
-    if (lane < m) x[k + 1 + lane] = xi - bt * s * vi;
+    if (lane < m) x[k + 1 + lane] = fma(-bt * s, vi, xi);
     __syncwarp();
   }
 }
 
-// Exact trust-region subproblem for one source; warp-cooperative.
-// Inputs g (27) and H (27 x 27) in global memory; writes p (smem y -> out).
-__device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* __restrict__ H,
-                         double Delta, double* __restrict__ p_out, double* pred_out, int lane) {
-  for (int e = lane; e < N * N; e += 32) {
+// Exact trust-region subproblem of one source; 128 threads (4 warps) enter,
+// warp 0 finishes: it returns true and holds p in S.y and the predicted
+// gain in S.red[0].  g (27) and H (27 x 27) are in global memory.
+__device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* __restrict__ H,
+                         double Delta) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < N * N; e += kTrThreads) {
     const int i = e / N, j = e % N;
     S.B[e] = -0.5 * (H[i * N + j] + H[j * N + i]);
   }
-  if (lane < N) S.gh[lane] = g[lane];
-  __syncwarp();
-  // ---- Householder tridiagonalisation; v_k stored below the diagonal
+  if (tid < N) S.gh[tid] = g[tid];
+  __syncthreads();
+  // ---- Householder tridiagonalisation; v_k stored below the diagonal of column k
   for (int k = 0; k < N - 2; ++k) {
     const int m = N - 1 - k;
-    const double xv = lane < m ? S.B[(k + 1 + lane) * N + k] : 0.0;
-    const double nrm2 = warp_sum_d(xv * xv);
-    const double x0 = __shfl_sync(0xffffffffu, xv, 0);
-    if (nrm2 - x0 * x0 <= 1e-300 || nrm2 == 0.0) {
-      if (lane == 0) {
-        S.beta[k] = 0.0;
-        S.d[k] = S.B[k * N + k];
-        S.e[k] = x0;
+    if (wid == 0) {
+      const double xv = lane < m ? S.B[(k + 1 + lane) * N + k] : 0.0;
+      const double nrm2 = warp_sum_d(xv * xv);
+      const double x0 = __shfl_sync(0xffffffffu, xv, 0);
+      const bool skip = nrm2 - x0 * x0 <= 1e-300 * fmax(nrm2, 1.0) || nrm2 == 0.0;
+      if (skip) {
+        if (lane == 0) {
+          S.beta[k] = 0.0;
+          S.d[k] = S.B[k * N + k];
+          S.e[k] = x0;
+        }
+      } else {
+        // alpha = -sign(x0) |x|;  v = x - alpha e_1;  beta = 2 / v.v = 1 / (|x|^2 - x0 alpha)
+        double r;
+        if (nrm2 > 1e-30 && nrm2 < 1e30) {
+          r = (double)rsqrtf((float)nrm2);                     // FP32 seed, then
+          r = r * fma(-0.5 * nrm2 * r, r, 1.5);                // two Newton steps
+          r = r * fma(-0.5 * nrm2 * r, r, 1.5);
+        } else {
+          r = rsqrt(nrm2);
+        }
+        const double alpha = -copysign(nrm2 * r, x0);
+        const double bt = 1.0 / fma(-x0, alpha, nrm2);
+        if (lane < m) S.B[(k + 1 + lane) * N + k] = xv - (lane == 0 ? alpha : 0.0);
+        if (lane == 0) {
+          S.beta[k] = bt;
+          S.d[k] = S.B[k * N + k];
+          S.e[k] = alpha;
+        }
       }
-      __syncwarp();
-      continue;
+      if (lane == 0) S.skip[k] = skip ? 1 : 0;
     }
-    const double alpha = -copysign(sqrt(nrm2), x0);
-    const double vv = xv - (lane == 0 ? alpha : 0.0);
-    const double vtv = warp_sum_d(vv * vv);
-    const double bt = 2.0 / vtv;
-    if (lane < m) S.B[(k + 1 + lane) * N + k] = vv;
-    __syncwarp();
-    double pi = 0.0;
+    __syncthreads();
+    if (S.skip[k]) continue;
+    // p = beta A22 v: rows over lanes, columns over the four warps
+    const int chunk = (m + 3) >> 2;
+    const int c0 = wid * chunk, c1 = min(m, c0 + chunk);
     if (lane < m) {
       const double* row = S.B + (k + 1 + lane) * N + k + 1;
-      for (int jj = 0; jj < m; ++jj) pi += row[jj] * S.B[(k + 1 + jj) * N + k];
-      pi *= bt;
+      double part = 0.0;
+      for (int c = c0; c < c1; ++c) part = fma(row[c], S.B[(k + 1 + c) * N + k], part);
+      S.part[wid * 32 + lane] = part;
     }
-    const double K = 0.5 * bt * warp_sum_d(vv * pi);
-    const double wi = pi - K * vv;
-    if (lane < m) S.w[lane] = wi;
-    __syncwarp();
+    __syncthreads();
+    if (wid == 0) {
+      const double bt = S.beta[k];
+      const double vv = lane < m ? S.B[(k + 1 + lane) * N + k] : 0.0;
+      const double pi = lane < m ? bt * (S.part[lane] + S.part[32 + lane] + S.part[64 + lane] +
+                                         S.part[96 + lane]) : 0.0;
+      const double K = 0.5 * bt * warp_sum_d(vv * pi);
+      if (lane < m) S.w[lane] = fma(-K, vv, pi);
+    }
+    __syncthreads();
+    // A22 -= v w^T + w v^T over the same (row, column chunk) split
     if (lane < m) {
       double* row = S.B + (k + 1 + lane) * N + k + 1;
-      for (int jj = 0; jj < m; ++jj) row[jj] -= vv * S.w[jj] + wi * S.B[(k + 1 + jj) * N + k];
+      const double vr = S.B[(k + 1 + lane) * N + k], wr = S.w[lane];
+      for (int c = c0; c < c1; ++c)
+        row[c] = fma(-vr, S.w[c], fma(-wr, S.B[(k + 1 + c) * N + k], row[c]));
     }
-    __syncwarp();
-    if (lane == 0) {
-      S.beta[k] = bt;
-      S.d[k] = S.B[k * N + k];
-      S.e[k] = alpha;
-    }
-    __syncwarp();
+    __syncthreads();
   }
+  if (wid != 0) return false;
   if (lane == 0) {
     S.d[N - 2] = S.B[(N - 2) * N + N - 2];
     S.d[N - 1] = S.B[(N - 1) * N + N - 1];
@@ -218,37 +255,36 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   }
   __syncwarp();
   apply_q(S, S.gh, true, lane);
-  const double* d = S.d;
-  const double* e = S.e;
-  const double* gh = S.gh;
-  double gn2 = 0.0, scale = 0.0;
+  // ---- scale: |T / scale| <= 1 (Gershgorin)
+  double scale = 0.0, gn2 = 0.0;
   for (int i = 0; i < N; ++i) {
-    gn2 += gh[i] * gh[i];
-    scale = fmax(scale, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : 0.0));
+    scale = fmax(scale, fabs(S.d[i]) + fabs(S.e[i]) + (i ? fabs(S.e[i - 1]) : 0.0));
+    gn2 = fma(S.gh[i], S.gh[i], gn2);
   }
   scale = fmax(scale, 1e-300);
   const double inv = 1.0 / scale;
-  // scaled copies: |T / scale| <= 1
   if (lane < N) {
-    S.df[lane] = (float)(d[lane] * inv);
-    S.ef[lane] = (float)(e[lane] * inv);
+    S.ds[lane] = S.d[lane] * inv;
+    S.es[lane] = S.e[lane] * inv;
+    S.gs[lane] = S.gh[lane] * inv;
+    S.df[lane] = (float)S.ds[lane];
+    S.ef[lane] = (float)S.es[lane];
     S.e2f[lane] = S.ef[lane] * S.ef[lane];
-    S.w[lane] = e[lane] * inv;      // FP64 scaled off-diagonal
-    S.z[lane] = d[lane] * inv;      // FP64 scaled diagonal
+    S.gf[lane] = (float)S.gs[lane];
   }
   __syncwarp();
-  // ---- lambda_min(T): FP32 multisection on the scaled matrix, then FP64
-  // multisection with the division-free Sturm sequence
+  const double* d = S.ds;
+  const double* e = S.es;
+  const double* gs = S.gs;
+  // ---- lambda_min of the scaled matrix
   double a = 1.0, b = -1.0;
   for (int i = 0; i < N; ++i) {
-    const double r = fabs(S.w[i]) + (i ? fabs(S.w[i - 1]) : 0.0);
-    a = fmin(a, S.z[i] - r);
-    b = fmax(b, S.z[i] + r);
+    const double r = fabs(e[i]) + (i ? fabs(e[i - 1]) : 0.0);
+    a = fmin(a, d[i] - r);
+    b = fmax(b, d[i] + r);
   }
-  a -= 1e-6;
-  b += 1e-6;
   {
-    float fa = (float)a, fb = (float)b;
+    float fa = (float)a - 1e-6f, fb = (float)b + 1e-6f;
     for (int round = 0; round < 5; ++round) {
       const float sig = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
       const bool hit = lane < 31 && sturm32(S.df, S.e2f, sig) >= 1;
@@ -260,58 +296,59 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
       fb = nb;
     }
     // FP32 counts are exact away from eigenvalues to ~1e-6 of the scale
-    a = fmax(a, (double)fa - 1e-5);
-    b = fmin(b, (double)fb + 1e-5);
+    a = fmax(a - 1e-6, (double)fa - 1e-5);
+    b = fmin(b + 1e-6, (double)fb + 1e-5);
   }
-  for (int round = 0; round < 5; ++round) {
-    const double sig = a + (b - a) * (double)(lane + 1) / 32.0;
-    const bool hit = lane < 31 && sturm64(S.z, S.w, sig) >= 1;
+  for (int round = 0; round < 4; ++round) {
+    const double sig = a + (b - a) * (double)(lane + 1) * (1.0 / 32.0);
+    const bool hit = lane < 31 && sturm64(d, e, sig) >= 1;
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int t = mask ? __ffs(mask) - 1 : 31;
-    const double na = t == 0 ? a : a + (b - a) * (double)t / 32.0;
-    const double nb = t == 31 ? b : a + (b - a) * (double)(t + 1) / 32.0;
+    const double na = t == 0 ? a : a + (b - a) * (double)t * (1.0 / 32.0);
+    const double nb = t == 31 ? b : a + (b - a) * (double)(t + 1) * (1.0 / 32.0);
     a = na;
     b = nb;
   }
-  const double lmin = 0.5 * (a + b) * scale;
-  // ---- multiplier
+  const double lmin = 0.5 * (a + b);    // scaled
+  // ---- multiplier (scaled units: l / scale); |y| is scale-invariant
   const double D2 = Delta * Delta;
-  double lam = 0.0;
-  bool interior = false, hard = false;
-  if (lmin > 0.0) interior = ldl_solve(d, e, gh, 0.0, nullptr, nullptr) <= D2;
-  if (!interior) {
+  bool done = false, hard = false;
+  if (lmin > 0.0) {
+    const double n2 = ldl_solve(d, e, gs, 0.0, S.y, nullptr);
+    done = n2 <= D2;
+  }
+  if (!done) {
     const double lo = fmax(0.0, -lmin);
-    const double eps = 1e-12 * scale;
+    const double eps = 1e-12;
     double la = lo + eps;
-    double lb = lo + sqrt(gn2) / Delta + eps;
-    if (ldl_solve(d, e, gh, la, nullptr, nullptr) <= D2) {
-      hard = true;
-      lam = la;
-    } else {
-      // FP32 multisection on the scaled problem for a starting point ...
-      if (lane < N) S.gf[lane] = (float)(gh[lane] * inv);
-      __syncwarp();
-      const float D2s = (float)(D2);          // |y| is scale-invariant
-      float fa = (float)(la * inv), fb = (float)(lb * inv);
-      for (int round = 0; round < 6; ++round) {
-        const float l = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
-        const bool inside = lane < 31 && norm2_32(S.df, S.ef, S.gf, l) <= D2s;
-        const unsigned mask = __ballot_sync(0xffffffffu, inside);
-        const int t = mask ? __ffs(mask) - 1 : 31;
-        const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
-        const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
-        fa = na;
-        fb = nb;
-      }
-      // ... then safeguarded Newton on 1/|y(l)| - 1/Delta in FP64
-      // (Nocedal & Wright, Algorithm 4.3), kept inside [la, lb]
-      double l = fmin(fmax((double)fb * scale, la), lb);
+    double lb = lo + sqrt(gn2) * inv / Delta + eps;
+    // FP32 multisection for a starting point; in the first round lane 31
+    // probes la itself (the hard-case test)
+    float fa = (float)la, fb = (float)lb;
+    bool low_inside = false;
+    for (int round = 0; round < 6; ++round) {
+      const float l = lane == 31 ? fa : fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
+      const bool inside = (lane < 31 || round == 0) && norm2_32(S.df, S.ef, S.gf, l) <= (float)D2;
+      const unsigned mask = __ballot_sync(0xffffffffu, inside);
+      if (round == 0) low_inside = (mask >> 31) != 0u;
+      const unsigned m2 = mask & 0x7fffffffu;
+      const int t = m2 ? __ffs(m2) - 1 : 31;
+      const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
+      const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
+      fa = na;
+      fb = nb;
+    }
+    if (low_inside) {
+      // possibly the hard case: decide in FP64 at the lowest admissible l
+      hard = ldl_solve(d, e, gs, la, S.y, nullptr) <= D2;
+    }
+    if (!hard) {
+      double l = fmin(fmax((double)fb, la), lb);
       for (int it = 0; it < 12; ++it) {
         double q;
-        const double n2 = ldl_solve(d, e, gh, l, nullptr, &q);
+        const double n2 = ldl_solve(d, e, gs, l, S.y, &q);
         const double ny = sqrt(n2);
         if (n2 <= D2) lb = l; else la = l;
-        lam = l;
         if (fabs(ny - Delta) <= 1e-13 * Delta) break;
         double ln = l + (ny - Delta) / Delta * n2 / q;
         if (!(ln > la && ln < lb)) ln = 0.5 * (la + lb);
@@ -320,99 +357,102 @@ __device__ void tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
       }
     }
   }
-  if (lane == 0) ldl_solve(d, e, gh, lam, S.y, nullptr);
   __syncwarp();
   if (hard) {
     // eigenvector of lambda_min by inverse iteration, shifted just below it
-    if (lane == 0) {
-      const double shift = -lmin + 1e-10 * scale;
-      for (int i = 0; i < N; ++i) S.w[i] = 1.0 / sqrt((double)N);
-      for (int itn = 0; itn < 4; ++itn) {
-        const double nz = ldl_solve(d, e, S.w, shift, S.z, nullptr);
-        const double r = 1.0 / sqrt(nz);
-        for (int i = 0; i < N; ++i) S.w[i] = S.z[i] * r;
-      }
-      // project z out of y
-      double zy = 0.0;
-      for (int i = 0; i < N; ++i) zy += S.w[i] * S.y[i];
-      for (int i = 0; i < N; ++i) {
-        S.y[i] -= zy * S.w[i];
-        S.z[i] = S.w[i];
-      }
+    const double shift = -lmin + 1e-10;
+    if (lane < N) S.w[lane] = 1.0 / sqrt((double)N);
+    __syncwarp();
+    for (int itn = 0; itn < 4; ++itn) {
+      const double nz = ldl_solve(d, e, S.w, shift, S.z, nullptr);
+      __syncwarp();
+      const double r = 1.0 / sqrt(nz);
+      if (lane < N) S.w[lane] = S.z[lane] * r;
+      __syncwarp();
+    }
+    double zy = 0.0;
+    for (int i = 0; i < N; ++i) zy = fma(S.w[i], S.y[i], zy);
+    __syncwarp();
+    if (lane < N) {
+      S.y[lane] = fma(-zy, S.w[lane], S.y[lane]);
+      S.z[lane] = S.w[lane];
     }
     __syncwarp();
     apply_q(S, S.z, false, lane);       // Q z, to fix the sign
-    if (lane == 0) {
-      double first = 0.0;
-      for (int i = 0; i < N; ++i) {
-        if (fabs(S.z[i]) > 1e-14) {
-          first = S.z[i];
-          break;
-        }
+    double first = 0.0;
+    for (int i = 0; i < N; ++i) {
+      if (fabs(S.z[i]) > 1e-14) {
+        first = S.z[i];
+        break;
       }
-      double ny2 = 0.0;
-      for (int i = 0; i < N; ++i) ny2 += S.y[i] * S.y[i];
-      const double tau = copysign(sqrt(fmax(D2 - ny2, 0.0)), first);
-      for (int i = 0; i < N; ++i) S.y[i] += tau * S.w[i];
     }
+    double ny2 = 0.0;
+    for (int i = 0; i < N; ++i) ny2 = fma(S.y[i], S.y[i], ny2);
+    const double tau = copysign(sqrt(fmax(D2 - ny2, 0.0)), first);
+    __syncwarp();
+    if (lane < N) S.y[lane] = fma(tau, S.w[lane], S.y[lane]);
     __syncwarp();
   }
-  // predicted gain in tridiagonal coordinates: y.gh - y.T.y / 2
+  // predicted gain: y.Q^T g - y.T.y / 2 (unscaled T)
   if (lane == 0) {
     double gy = 0.0, yty = 0.0;
     for (int i = 0; i < N; ++i) {
       const double yi = S.y[i];
-      gy += yi * gh[i];
-      double ty = d[i] * yi;
-      if (i > 0) ty += e[i - 1] * S.y[i - 1];
-      if (i < N - 1) ty += e[i] * S.y[i + 1];
-      yty += yi * ty;
+      gy = fma(yi, S.gh[i], gy);
+      double ty = S.d[i] * yi;
+      if (i > 0) ty = fma(S.e[i - 1], S.y[i - 1], ty);
+      if (i < N - 1) ty = fma(S.e[i], S.y[i + 1], ty);
+      yty = fma(yi, ty, yty);
     }
     S.red[0] = gy - 0.5 * yty;
   }
   __syncwarp();
   apply_q(S, S.y, false, lane);
-  if (lane < N) p_out[lane] = S.y[lane];
-  if (pred_out && lane == 0) *pred_out = S.red[0];
-  __syncwarp();
+  return true;
 }
 
-__global__ void tr_subproblem_kernel(int n, const double* g, const double* H, const double* delta,
-                                     double* p, double* pred) {
+__global__ void __launch_bounds__(kTrThreads) tr_subproblem_kernel(int n, const double* g,
+                                                                  const double* H,
+                                                                  const double* delta, double* p,
+                                                                  double* pred) {
   extern __shared__ double smd[];
   TrSmem& S = *reinterpret_cast<TrSmem*>(smd);
   const int j = blockIdx.x;
   if (j >= n) return;
-  tr_solve(S, g + (size_t)j * N, H + (size_t)j * N * N, delta[j], p + (size_t)j * N, pred + j,
-           threadIdx.x);
+  if (!tr_solve(S, g + (size_t)j * N, H + (size_t)j * N * N, delta[j])) return;
+  const int lane = threadIdx.x & 31;
+  if (lane < N) p[(size_t)j * N + lane] = S.y[lane];
+  if (lane == 0) pred[j] = S.red[0];
 }
 
 // Step of every active slot: converged sources leave the active set.
-__global__ void tr_step_kernel(PlanView v, const double* delta, int32_t* status) {
+__global__ void __launch_bounds__(kTrThreads) tr_step_kernel(PlanView v, const double* delta,
+                                                            int32_t* status) {
   extern __shared__ double smd[];
   TrSmem& S = *reinterpret_cast<TrSmem*>(smd);
   const int j = blockIdx.x;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (!v.active[j]) return;
   const int src = v.src_ids[j];
   const double Dl = delta[src];
   const double* g = v.grad + (size_t)j * N;
   const double* H = v.hess + (size_t)j * N * N;
   bool finite = true;
-  for (int e = lane; e < N * N; e += 32) finite &= isfinite(H[e]);
-  if (lane < N) finite &= isfinite(g[lane]);
-  finite = __all_sync(0xffffffffu, finite) && isfinite(v.elbo_rel[j]);
+  for (int e = tid; e < N * N; e += kTrThreads) finite &= isfinite(H[e]);
+  if (tid < N) finite &= isfinite(g[tid]);
+  finite = __syncthreads_and(finite) && isfinite(v.elbo_rel[j]);
   if (!finite) {
-    if (lane == 0) {
+    if (tid == 0) {
       status[src] = CELESTE_ST_FAILED;
       v.active[j] = 0;
     }
     return;
   }
+  if (!tr_solve(S, g, H, Dl)) return;
   double* p = v.step + (size_t)j * N;
-  tr_solve(S, g, H, Dl, p, v.pred + j, lane);
-  __syncwarp();
-  const double pred = v.pred[j];
+  if (lane < N) p[lane] = S.y[lane];
+  const double pred = S.red[0];
+  if (lane == 0) v.pred[j] = pred;
   if (pred <= kFtol * (1.0 + fabs(v.elbo_rel[j])) || Dl < kDeltaMin) {
     if (lane == 0) {
       status[src] = CELESTE_ST_CONVERGED;
@@ -420,7 +460,7 @@ __global__ void tr_step_kernel(PlanView v, const double* delta, int32_t* status)
     }
     return;
   }
-  if (lane < N) v.theta_trial[(size_t)j * N + lane] = v.theta[(size_t)src * N + lane] + p[lane];
+  if (lane < N) v.theta_trial[(size_t)j * N + lane] = v.theta[(size_t)src * N + lane] + S.y[lane];
 }
 
 // Accept or reject the trial points; update radius and status.
@@ -431,7 +471,7 @@ __global__ void tr_accept_kernel(PlanView v, const double* __restrict__ rel_tria
   const int src = v.src_ids[j];
   const double* p = v.step + (size_t)j * N;
   double pn = 0.0;
-  for (int i = 0; i < N; ++i) pn += p[i] * p[i];
+  for (int i = 0; i < N; ++i) pn = fma(p[i], p[i], pn);
   pn = sqrt(pn);
   const double Dl = delta[src];
   const double actual = rel_trial[j] - v.elbo_rel[j];
@@ -469,7 +509,7 @@ cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const 
                                  const double* delta, double* p, double* pred) {
   if (n <= 0) return cudaSuccess;
   set_attrs();
-  tr_subproblem_kernel<<<n, 32, sizeof(TrSmem), L.stream>>>(n, g, H, delta, p, pred);
+  tr_subproblem_kernel<<<n, kTrThreads, sizeof(TrSmem), L.stream>>>(n, g, H, delta, p, pred);
   return cudaGetLastError();
 }
 
@@ -477,7 +517,7 @@ cudaError_t launch_tr_step(const Launch& L, const PlanView& v, const double* del
                            int32_t* status) {
   if (v.n <= 0) return cudaSuccess;
   set_attrs();
-  tr_step_kernel<<<v.n, 32, sizeof(TrSmem), L.stream>>>(v, delta, status);
+  tr_step_kernel<<<v.n, kTrThreads, sizeof(TrSmem), L.stream>>>(v, delta, status);
   return cudaGetLastError();
 }
 

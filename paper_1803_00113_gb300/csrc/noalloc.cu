@@ -51,76 +51,6 @@ static ModelDev h_model;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Inverse and log-determinant of a symmetric positive-definite 4 x 4 matrix.
-bool inverse4_spd(const double C[4][4], double P[4][4], double* logdet) {
-  double L[4][4] = {{0}};
-  double ld = 0.0;
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = C[i][j];
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-      if (i == j) {
-        if (!(s > 0.0)) return false;
-        L[i][i] = sqrt(s);
-        ld += 2.0 * log(L[i][i]);
-      } else {
-        L[i][j] = s / L[j][j];
-      }
-    }
-  // solve L L^T P = I column by column
-  for (int c = 0; c < 4; ++c) {
-    double y[4];
-    for (int i = 0; i < 4; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-      y[i] = s / L[i][i];
-    }
-    for (int i = 3; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < 4; ++k) s -= L[k][i] * P[k][c];
-      P[i][c] = s / L[i][i];
-    }
-  }
-  *logdet = ld;
-  return true;
-}
-
-bool prepare_model(const celeste_model* m, ModelDev* md) {
-  if (m->n_exp < 1 || m->n_exp > kMaxProf || m->n_dev < 1 || m->n_dev > kMaxProf ||
-      m->n_color < 1 || m->n_color > kMaxColor || !(m->prior_a > 0.0 && m->prior_a < 1.0) ||
-      !(m->e_radius[1] > 0.0))
-    return false;
-  memset(md, 0, sizeof(*md));
-  md->n_exp = m->n_exp;
-  md->n_dev = m->n_dev;
-  md->n_color = m->n_color;
-  for (int j = 0; j < kMaxProf; ++j) {
-    md->alpha_exp[j] = m->alpha_exp[j];
-    md->tau_exp[j] = m->tau_exp[j];
-    md->alpha_dev[j] = m->alpha_dev[j];
-    md->tau_dev[j] = m->tau_dev[j];
-  }
-  md->prior_a = m->prior_a;
-  for (int i = 0; i < 2; ++i) {
-    if (!(m->prior_r[i][1] > 0.0)) return false;
-    md->prior_r[i][0] = m->prior_r[i][0];
-    md->prior_r[i][1] = m->prior_r[i][1];
-    for (int j = 0; j < m->n_color; ++j) {
-      if (!(m->color_w[i][j] > 0.0)) return false;
-      md->color_w[i][j] = m->color_w[i][j];
-      for (int k = 0; k < 4; ++k) md->color_mean[i][j][k] = m->color_mean[i][j][k];
-      if (!inverse4_spd(m->color_cov[i][j], md->color_prec[i][j], &md->color_logdet[i][j]))
-        return false;
-    }
-  }
-  for (int k = 0; k < 2; ++k) {
-    md->e_radius[k] = m->e_radius[k];
-    md->e_profile[k] = m->e_profile[k];
-    md->e_axis[k] = m->e_axis[k];
-  }
-  return true;
-}
-
 // Once per device, with that device current: the device address of the
 // scratch array (the array's name in host code is only a stand-in).
 int device_setup(int dev, DeviceSetup** out) {
