@@ -16,15 +16,19 @@
 // KL_s follows Eq. kleq, Supplement A and the GMM colour bound of Sec. 4.2.3
 // with xi minimised in closed form: -log sum_j w_j exp(-KL(q(c|a) || N_j)).
 //
-// GB300 issues a warp-wide FP64 instruction in ~19 cycles, so FP64 is kept
-// to the reductions, the chain rule and the KL, and those are spread over
-// the lanes (the per-image affine maps run in FP32: each of their products
-// is a reduced sum times a near-identity constant).
+// Precision: the inputs of the chain rule are sums accumulated in FP32 by
+// the pixel kernel, so the chain rule and the KL run in FP32 ("real"), which
+// adds rounding of the same order as its inputs already carry; the value
+// sums (which include the large sky baseline) stay in FP64.  On GB300 an
+// FP64 instruction costs ~64 cycles per SM sub-partition, and this kernel
+// is on the critical path of every colour class.
 #include <math.h>
 
 #include "internal.cuh"
 
 namespace celeste {
+
+typedef float real;
 
 __constant__ signed char kSelE[5][4] = {
     {-1, -1, 0, 0}, {0, -1, 0, 0}, {0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 1, 1}};
@@ -33,33 +37,29 @@ constexpr int kNu = 26;   // 20 flux moments (band b, kind e at 4b+e), u (2), Si
 constexpr int kNuPad = 32;
 constexpr int kKlVals = 8 + 36 + 10 + 4;   // per colour component: grad, outer, prec, diag
 
-// Transcendentals of single parameters run in FP32 (relative error ~1e-7,
-// far inside the tolerances); the arithmetic that combines them stays FP64.
-__device__ __forceinline__ double sigm(double t) {
-  const float f = (float)t;
-  return (double)(f >= 0.f ? 1.f / (1.f + expf(-f)) : expf(f) / (1.f + expf(f)));
+__device__ __forceinline__ real sigm(real t) {
+  return t >= 0.f ? 1.f / (1.f + expf(-t)) : expf(t) / (1.f + expf(t));
 }
 // log(1 + exp(t)) without overflow
-__device__ __forceinline__ double softplus(double t) {
-  const float f = (float)t;
-  return (double)(f > 0.f ? f + log1pf(expf(-f)) : log1pf(expf(f)));
+__device__ __forceinline__ real softplus(real t) {
+  return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t));
 }
-__device__ __forceinline__ double exp1(double t) { return (double)expf((float)t); }
 
 struct EpiSmem {
   double W[kAcc];                  // one pair's sums
-  double gnu[kNuPad];
-  double Hnu[kNu * kNu];
-  double J[kNu * kTheta];
-  double X[kNu * kTheta];
-  double gth[kNuPad];
-  double Hth[kTheta * kTheta];
-  double DL[20 * kTheta];          // d log kappa_a / d theta
-  double D2L[20 * kTheta];         // diagonal second derivatives of log kappa_a
-  double kw[kNuPad];               // grad_nu[a] * kappa_a
-  double klc[2 * kMaxColor * kKlVals];   // colour-bound pieces per (type, component)
-  double klj[2 * kMaxColor];       // log w_j - K_j
-  double kls[8];                   // scalar KL pieces
+  real th[kNuPad];                 // theta of the source (FP32 copy)
+  real gnu[kNuPad];
+  real Hnu[kNu * kNu];
+  real J[kNu * kTheta];
+  real X[kNu * kTheta];
+  real gth[kNuPad];
+  real Hth[kTheta * kTheta];
+  real DL[20 * kTheta];            // d log kappa_a / d theta
+  real D2L[20 * kTheta];           // diagonal second derivatives of log kappa_a
+  real kw[kNuPad];                 // grad_nu[a] * kappa_a
+  real klc[2 * kMaxColor * kKlVals];   // colour-bound pieces per (type, component)
+  real klj[2 * kMaxColor];         // log w_j - K_j
+  real kls[8];                     // scalar KL pieces
   float T[10 * 10];                // per-image affine map w <- nu (local)
 };
 
@@ -83,66 +83,65 @@ __device__ __forceinline__ int col_rows(int c, int* rows) {
 
 // d log kappa / d theta for flux-moment coordinate a (0..19): band b = a / 4,
 // kind e = a % 4 (0: kE0, 1: kE1, 2: kM0, 3: kM1).  Returns kappa.
-__device__ double kappa_logderivs(const double* th, int a, double* dl, double* d2l) {
+__device__ real kappa_logderivs(const real* th, int a, real* dl, real* d2l) {
   const int b = a >> 2, e = a & 3;
   const int i = e & 1;
   const bool second = e >= 2;
-  const double am = second ? 2.0 : 1.0, av = second ? 2.0 : 0.5;
-  for (int c = 0; c < kTheta; ++c) dl[c] = d2l[c] = 0.0;
-  const double q1 = sigm(th[0]), q0 = sigm(-th[0]);
-  const double logq = i ? -softplus(-th[0]) : -softplus(th[0]);
+  const real am = second ? 2.f : 1.f, av = second ? 2.f : 0.5f;
+  for (int c = 0; c < kTheta; ++c) dl[c] = d2l[c] = 0.f;
+  const real q1 = sigm(th[0]), q0 = sigm(-th[0]);
+  const real logq = i ? -softplus(-th[0]) : -softplus(th[0]);
   dl[0] = i ? q0 : -q1;
   d2l[0] = -q0 * q1;
   const int ir = 1 + 2 * i, iv = 2 + 2 * i;
-  double m = th[ir], v = exp1(th[iv]);
+  real m = th[ir], v = expf(th[iv]);
   dl[ir] = am;
   dl[iv] = av * v;
   d2l[iv] = dl[iv];
   for (int k = 0; k < 4; ++k) {
-    const double s = (double)kSelE[b][k];
-    const double cvk = exp1(th[13 + 4 * i + k]);
+    const real s = (real)kSelE[b][k];
+    const real cvk = expf(th[13 + 4 * i + k]);
     m += s * th[5 + 4 * i + k];
     v += s * s * cvk;
     dl[5 + 4 * i + k] = am * s;
     dl[13 + 4 * i + k] = av * s * s * cvk;
     d2l[13 + 4 * i + k] = dl[13 + 4 * i + k];
   }
-  return exp1(logq + am * m + av * v);
+  return expf(logq + am * m + av * v);
 }
 
 // Derivatives of Sigma_s = (S11, S12, S22) over (angle, log radius, logit axis).
-__device__ void sigma_derivs(const double* th, double dS[3][3], double d2S[3][3][3]) {
-  const double phi = th[23], lr = th[24];
-  const double ax = sigm(th[25]);
-  const double e2 = exp1(2.0 * lr);
-  const double a2 = ax * ax;
-  const double a2t = 2.0 * a2 * (1.0 - ax);
-  const double a2tt = 2.0 * a2 * (1.0 - ax) * (2.0 - 3.0 * ax);
-  const double P = 0.5 * e2 * (1.0 + a2), Qd = 0.5 * e2 * (1.0 - a2);
-  const double Pl = 2.0 * P, Pll = 4.0 * P, Pt = 0.5 * e2 * a2t, Ptt = 0.5 * e2 * a2tt, Plt = 2.0 * Pt;
-  const double Ql = 2.0 * Qd, Qll = 4.0 * Qd, Qt = -0.5 * e2 * a2t, Qtt = -0.5 * e2 * a2tt, Qlt = 2.0 * Qt;
-  float s2f, c2f;
-  sincosf((float)(2.0 * phi), &s2f, &c2f);
-  const double C2 = c2f, S2 = s2f;
+__device__ void sigma_derivs(const real* th, real dS[3][3], real d2S[3][3][3]) {
+  const real phi = th[23], lr = th[24];
+  const real ax = sigm(th[25]);
+  const real e2 = expf(2.f * lr);
+  const real a2 = ax * ax;
+  const real a2t = 2.f * a2 * (1.f - ax);
+  const real a2tt = 2.f * a2 * (1.f - ax) * (2.f - 3.f * ax);
+  const real P = 0.5f * e2 * (1.f + a2), Qd = 0.5f * e2 * (1.f - a2);
+  const real Pl = 2.f * P, Pll = 4.f * P, Pt = 0.5f * e2 * a2t, Ptt = 0.5f * e2 * a2tt, Plt = 2.f * Pt;
+  const real Ql = 2.f * Qd, Qll = 4.f * Qd, Qt = -0.5f * e2 * a2t, Qtt = -0.5f * e2 * a2tt, Qlt = 2.f * Qt;
+  real S2, C2;
+  sincosf(2.f * phi, &S2, &C2);
   // S11 = P + Qd C2, S22 = P - Qd C2, S12 = -Qd S2
   for (int e = 0; e < 3; e += 2) {
-    const double s = e == 0 ? 1.0 : -1.0;
-    dS[e][0] = -2.0 * s * Qd * S2;
+    const real s = e == 0 ? 1.f : -1.f;
+    dS[e][0] = -2.f * s * Qd * S2;
     dS[e][1] = Pl + s * Ql * C2;
     dS[e][2] = Pt + s * Qt * C2;
-    d2S[e][0][0] = -4.0 * s * Qd * C2;
-    d2S[e][0][1] = d2S[e][1][0] = -2.0 * s * Ql * S2;
-    d2S[e][0][2] = d2S[e][2][0] = -2.0 * s * Qt * S2;
+    d2S[e][0][0] = -4.f * s * Qd * C2;
+    d2S[e][0][1] = d2S[e][1][0] = -2.f * s * Ql * S2;
+    d2S[e][0][2] = d2S[e][2][0] = -2.f * s * Qt * S2;
     d2S[e][1][1] = Pll + s * Qll * C2;
     d2S[e][1][2] = d2S[e][2][1] = Plt + s * Qlt * C2;
     d2S[e][2][2] = Ptt + s * Qtt * C2;
   }
-  dS[1][0] = -2.0 * Qd * C2;
+  dS[1][0] = -2.f * Qd * C2;
   dS[1][1] = -Ql * S2;
   dS[1][2] = -Qt * S2;
-  d2S[1][0][0] = 4.0 * Qd * S2;
-  d2S[1][0][1] = d2S[1][1][0] = -2.0 * Ql * C2;
-  d2S[1][0][2] = d2S[1][2][0] = -2.0 * Qt * C2;
+  d2S[1][0][0] = 4.f * Qd * S2;
+  d2S[1][0][1] = d2S[1][1][0] = -2.f * Ql * C2;
+  d2S[1][0][2] = d2S[1][2][0] = -2.f * Qt * C2;
   d2S[1][1][1] = -Qll * S2;
   d2S[1][1][2] = d2S[1][2][1] = -Qlt * S2;
   d2S[1][2][2] = -Qtt * S2;
@@ -151,47 +150,47 @@ __device__ void sigma_derivs(const double* th, double dS[3][3], double d2S[3][3]
 // KL_s: value into S.kls[0]; with kDerivs, gradient and Hessian are
 // ADDED (with a minus sign, since L = ... - KL) into S.gth and S.Hth.
 template <bool kDerivs>
-__device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int lane) {
-  const double a = sigm(th[0]);
-  const double wq = a * (1.0 - a);
+__device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane) {
+  const real a = sigm(th[0]);
+  const real wq = a * (1.f - a);
   const int J = m->n_color;
   // ---- colour bound, one lane per (type, component)
   if (lane < 2 * kMaxColor) {
     const int i = lane / kMaxColor, j = lane % kMaxColor;
     if (j < J) {
       const double(*P)[4] = m->color_prec[i][j];
-      const double* cm = th + 5 + 4 * i;
-      const double* lcv = th + 13 + 4 * i;
-      double d[4], cv[4], pd[4];
-      double tr = 0.0, quad = 0.0, slv = 0.0;
+      const real* cm = th + 5 + 4 * i;
+      const real* lcv = th + 13 + 4 * i;
+      real d[4], cv[4], pd[4];
+      real tr = 0.f, quad = 0.f, slv = 0.f;
       for (int k = 0; k < 4; ++k) {
-        d[k] = cm[k] - m->color_mean[i][j][k];
-        cv[k] = exp1(lcv[k]);
+        d[k] = cm[k] - (real)m->color_mean[i][j][k];
+        cv[k] = expf(lcv[k]);
       }
       for (int k = 0; k < 4; ++k) {
-        double s = 0.0;
-        for (int l = 0; l < 4; ++l) s += P[k][l] * d[l];
+        real s = 0.f;
+        for (int l = 0; l < 4; ++l) s = fmaf((real)P[k][l], d[l], s);
         pd[k] = s;
-        tr += P[k][k] * cv[k];
-        quad += d[k] * s;
+        tr = fmaf((real)P[k][k], cv[k], tr);
+        quad = fmaf(d[k], s, quad);
         slv += lcv[k];
       }
-      const double K = 0.5 * (tr + quad - 4.0 + m->color_logdet[i][j] - slv);
-      S.klj[lane] = m->log_color_w[i][j] - K;
+      const real K = 0.5f * (tr + quad - 4.f + (real)m->color_logdet[i][j] - slv);
+      S.klj[lane] = (real)m->log_color_w[i][j] - K;
       if (kDerivs) {
-        double* o = S.klc + lane * kKlVals;
-        double gk[8];
+        real* o = S.klc + lane * kKlVals;
+        real gk[8];
         for (int k = 0; k < 4; ++k) {
           gk[k] = pd[k];
-          gk[4 + k] = 0.5 * (P[k][k] * cv[k] - 1.0);
+          gk[4 + k] = 0.5f * ((real)P[k][k] * cv[k] - 1.f);
         }
         for (int k = 0; k < 8; ++k) o[k] = gk[k];
         int t = 8;
         for (int k = 0; k < 8; ++k)
           for (int l = k; l < 8; ++l) o[t++] = gk[k] * gk[l];
         for (int k = 0; k < 4; ++k)
-          for (int l = k; l < 4; ++l) o[t++] = P[k][l];
-        for (int k = 0; k < 4; ++k) o[t++] = 0.5 * P[k][k] * cv[k];
+          for (int l = k; l < 4; ++l) o[t++] = (real)P[k][l];
+        for (int k = 0; k < 4; ++k) o[t++] = 0.5f * (real)P[k][k] * cv[k];
       }
     } else {
       S.klj[lane] = -INFINITY;
@@ -201,47 +200,48 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   // ---- per type: softmax weights pi_j = w_j exp(-K_j) / sum (one exp per lane)
   if (lane < 2 * kMaxColor) {
     const int i = lane / kMaxColor;
-    double mx = -INFINITY;
-    for (int j = 0; j < J; ++j) mx = fmax(mx, S.klj[i * kMaxColor + j]);
-    S.kw[lane] = (lane % kMaxColor) < J ? exp1(S.klj[lane] - mx) : 0.0;   // scratch
+    real mx = -INFINITY;
+    for (int j = 0; j < J; ++j) mx = fmaxf(mx, S.klj[i * kMaxColor + j]);
+    S.kw[lane] = (lane % kMaxColor) < J ? expf(S.klj[lane] - mx) : 0.f;   // scratch
     S.kls[4 + i] = mx;
   }
   __syncwarp();
-  double Bval[2], se[2];
+  real Bval[2], se[2];
   for (int i = 0; i < 2; ++i) {
-    se[i] = 0.0;
+    se[i] = 0.f;
     for (int j = 0; j < J; ++j) se[i] += S.kw[i * kMaxColor + j];
-    Bval[i] = -(S.kls[4 + i] + (double)logf((float)se[i]));
+    Bval[i] = -(S.kls[4 + i] + logf(se[i]));
   }
   if (kDerivs) {
     // pi-weighted sums of the per-component pieces, per type (lanes over values)
     for (int e = lane; e < 2 * kKlVals; e += 32) {
       const int i = e / kKlVals, vv = e % kKlVals;
-      double acc = 0.0;
+      real acc = 0.f;
       for (int j = 0; j < J; ++j)
-        acc += S.kw[i * kMaxColor + j] * S.klc[(i * kMaxColor + j) * kKlVals + vv];
+        acc = fmaf(S.kw[i * kMaxColor + j], S.klc[(i * kMaxColor + j) * kKlVals + vv], acc);
       S.X[i * 64 + vv] = acc / se[i];   // scratch
     }
   }
   __syncwarp();
-  // ---- assemble (lane 0 for the value, lanes over entries for the derivatives)
+  // ---- value (lane 0)
   if (lane == 0) {
-    double v = a * (-softplus(-th[0]) - m->log_prior_a) + (1.0 - a) * (-softplus(th[0]) - m->log1m_prior_a);
+    real v = a * (-softplus(-th[0]) - (real)m->log_prior_a) +
+             (1.f - a) * (-softplus(th[0]) - (real)m->log1m_prior_a);
     for (int i = 0; i < 2; ++i) {
-      const double R1 = m->prior_r[i][0], R2 = m->prior_r[i][1];
-      const double rm = th[1 + 2 * i], lrv = th[2 + 2 * i], rv = exp1(lrv);
-      const double klr = 0.5 * (m->log_prior_r2[i] - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.0);
+      const real R1 = (real)m->prior_r[i][0], R2 = (real)m->prior_r[i][1];
+      const real rm = th[1 + 2 * i], lrv = th[2 + 2 * i], rv = expf(lrv);
+      const real klr = 0.5f * ((real)m->log_prior_r2[i] - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.f);
       S.kls[2 + i] = klr + Bval[i];
-      v += (i ? a : 1.0 - a) * S.kls[2 + i];
+      v += (i ? a : 1.f - a) * S.kls[2 + i];
     }
-    const double lr = th[24], E1 = m->e_radius[0], E2 = m->e_radius[1];
-    v += lr + m->half_log_2pi_e2 + (lr - E1) * (lr - E1) / (2.0 * E2);
+    const real lr = th[24], E1 = (real)m->e_radius[0], E2 = (real)m->e_radius[1];
+    v += lr + (real)m->half_log_2pi_e2 + (lr - E1) * (lr - E1) / (2.f * E2);
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
-      const double b1 = which ? m->e_profile[0] : m->e_axis[0];
-      const double b2 = which ? m->e_profile[1] : m->e_axis[1];
-      v += (b1 - 1.0) * softplus(-th[t]) + (b2 - 1.0) * softplus(th[t]) +
-           (which ? m->log_beta_profile : m->log_beta_axis);
+      const real b1 = (real)(which ? m->e_profile[0] : m->e_axis[0]);
+      const real b2 = (real)(which ? m->e_profile[1] : m->e_axis[1]);
+      v += (b1 - 1.f) * softplus(-th[t]) + (b2 - 1.f) * softplus(th[t]) +
+           (real)(which ? m->log_beta_profile : m->log_beta_axis);
     }
     S.kls[0] = v;
   }
@@ -254,19 +254,19 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   };
   for (int e = lane; e < 2 * 100; e += 32) {
     const int i = e / 100, k = (e % 100) / 10, l = e % 10;
-    const double* pw = S.X + i * 64;            // pi-weighted: grad(8), outer(36), prec(10), diag(4)
-    const double R2 = m->prior_r[i][1];
-    const double rm = th[1 + 2 * i], rv = exp1(th[2 + 2 * i]);
+    const real* pw = S.X + i * 64;            // pi-weighted: grad(8), outer(36), prec(10), diag(4)
+    const real R2 = (real)m->prior_r[i][1];
+    const real rm = th[1 + 2 * i], rv = expf(th[2 + 2 * i]);
     // gradient of K_i = KL_r + B at local k
     auto gK = [&](int kk) {
-      if (kk == 0) return (rm - m->prior_r[i][0]) / R2;
-      if (kk == 1) return 0.5 * (rv / R2 - 1.0);
+      if (kk == 0) return (rm - (real)m->prior_r[i][0]) / R2;
+      if (kk == 1) return 0.5f * (rv / R2 - 1.f);
       return pw[kk - 2];
     };
-    double h = 0.0;
+    real h = 0.f;
     if (k < 2 || l < 2) {
-      if (k == l && k == 0) h = 1.0 / R2;
-      if (k == l && k == 1) h = 0.5 * rv / R2;
+      if (k == l && k == 0) h = 1.f / R2;
+      if (k == l && k == 1) h = 0.5f * rv / R2;
     } else {
       const int u = k - 2, w = l - 2;        // colour block 0..7
       const int lo = u < w ? u : w, hi = u < w ? w : u;
@@ -280,11 +280,11 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
         h += pw[54 + (u - 4)];
       }
     }
-    const double qi = i ? a : 1.0 - a;
+    const real qi = i ? a : 1.f - a;
     S.Hth[tidx(i, k) * kTheta + tidx(i, l)] -= qi * h;
     if (l == 0) {
-      const double dq = i ? wq : -wq;
-      const double g = gK(k);
+      const real dq = i ? wq : -wq;
+      const real g = gK(k);
       S.gth[tidx(i, k)] -= qi * g;
       S.Hth[tidx(i, k) * kTheta + 0] -= dq * g;
       S.Hth[0 * kTheta + tidx(i, k)] -= dq * g;
@@ -292,20 +292,20 @@ __device__ void kl_terms(const double* th, const ModelDev* m, EpiSmem& S, int la
   }
   __syncwarp();
   if (lane == 0) {
-    const double la = m->logit_prior_a;
-    const double d2q = wq * (1.0 - 2.0 * a);
+    const real la = (real)m->logit_prior_a;
+    const real d2q = wq * (1.f - 2.f * a);
     S.gth[0] -= wq * (th[0] - la) + wq * (S.kls[3] - S.kls[2]);
-    S.Hth[0] -= wq * ((1.0 - 2.0 * a) * (th[0] - la) + 1.0) + d2q * (S.kls[3] - S.kls[2]);
-    const double lr = th[24], E1 = m->e_radius[0], E2 = m->e_radius[1];
-    S.gth[24] -= 1.0 + (lr - E1) / E2;
-    S.Hth[24 * kTheta + 24] -= 1.0 / E2;
+    S.Hth[0] -= wq * ((1.f - 2.f * a) * (th[0] - la) + 1.f) + d2q * (S.kls[3] - S.kls[2]);
+    const real lr = th[24], E1 = (real)m->e_radius[0], E2 = (real)m->e_radius[1];
+    S.gth[24] -= 1.f + (lr - E1) / E2;
+    S.Hth[24 * kTheta + 24] -= 1.f / E2;
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
-      const double b1 = which ? m->e_profile[0] : m->e_axis[0];
-      const double b2 = which ? m->e_profile[1] : m->e_axis[1];
-      const double sg = sigm(th[t]);
-      S.gth[t] -= -(b1 - 1.0) * (1.0 - sg) + (b2 - 1.0) * sg;
-      S.Hth[t * kTheta + t] -= (b1 + b2 - 2.0) * sg * (1.0 - sg);
+      const real b1 = (real)(which ? m->e_profile[0] : m->e_axis[0]);
+      const real b2 = (real)(which ? m->e_profile[1] : m->e_axis[1]);
+      const real sg = sigm(th[t]);
+      S.gth[t] -= -(b1 - 1.f) * (1.f - sg) + (b2 - 1.f) * sg;
+      S.Hth[t * kTheta + t] -= (b1 + b2 - 2.f) * sg * (1.f - sg);
     }
   }
   __syncwarp();
@@ -321,14 +321,16 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   const int lane = threadIdx.x;
   if (!v.active[j]) return;
   const int src = v.src_ids[j];
-  const double* th = use_trial ? v.theta_trial + (size_t)j * kTheta : v.theta + (size_t)src * kTheta;
+  const double* thd = use_trial ? v.theta_trial + (size_t)j * kTheta : v.theta + (size_t)src * kTheta;
+  if (lane < kTheta) S.th[lane] = (real)thd[lane];
+  const real* th = S.th;
 
   double vrel = 0.0, vbase = 0.0;
   if (kDerivs) {
-    for (int e = lane; e < kNuPad; e += 32) S.gnu[e] = 0.0;
-    for (int e = lane; e < kNu * kNu; e += 32) S.Hnu[e] = 0.0;
-    for (int e = lane; e < kNuPad; e += 32) S.gth[e] = 0.0;
-    for (int e = lane; e < kTheta * kTheta; e += 32) S.Hth[e] = 0.0;
+    for (int e = lane; e < kNuPad; e += 32) S.gnu[e] = 0.f;
+    for (int e = lane; e < kNu * kNu; e += 32) S.Hnu[e] = 0.f;
+    for (int e = lane; e < kNuPad; e += 32) S.gth[e] = 0.f;
+    for (int e = lane; e < kTheta * kTheta; e += 32) S.Hth[e] = 0.f;
   }
   __syncwarp();
   for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
@@ -378,7 +380,7 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
     if (lane < 10) {
       float gl = 0.f;
       for (int k = lo(lane); k < hi(lane); ++k) gl += S.T[k * 10 + lane] * (float)S.W[2 + k];
-      S.gnu[nu_of(lane)] += (double)gl;
+      S.gnu[nu_of(lane)] += gl;
     }
     for (int e = lane; e < 55; e += 32) {
       int a = 0, rem = e;
@@ -393,8 +395,8 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
           val = fmaf(S.T[k * 10 + a] * S.T[l * 10 + c], hwv, val);
         }
       const int na = nu_of(a), nc = nu_of(c);
-      S.Hnu[na * kNu + nc] += (double)val;
-      if (na != nc) S.Hnu[nc * kNu + na] += (double)val;
+      S.Hnu[na * kNu + nc] += val;
+      if (na != nc) S.Hnu[nc * kNu + na] += val;
     }
     vrel += S.W[0];
     vbase += S.W[1];
@@ -402,48 +404,48 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   }
 
   kl_terms<kDerivs>(th, model, S, lane);
-  const double kl = S.kls[0];
+  const double kl = (double)S.kls[0];
   if (kDerivs) {
     // Jacobian rows: flux moments (lanes 0..19), u, Sigma_s, rho
-    for (int e = lane; e < kNu * kTheta; e += 32) S.J[e] = 0.0;
+    for (int e = lane; e < kNu * kTheta; e += 32) S.J[e] = 0.f;
     __syncwarp();
     if (lane < 20) {
-      double* dl = S.DL + lane * kTheta;
-      double* d2l = S.D2L + lane * kTheta;
-      const double kap = kappa_logderivs(th, lane, dl, d2l);
+      real* dl = S.DL + lane * kTheta;
+      real* d2l = S.D2L + lane * kTheta;
+      const real kap = kappa_logderivs(th, lane, dl, d2l);
       for (int c = 0; c < kTheta; ++c) S.J[lane * kTheta + c] = kap * dl[c];
       S.kw[lane] = S.gnu[lane] * kap;
     } else if (lane < 22) {
-      S.J[lane * kTheta + 21 + (lane - 20)] = 1.0;
+      S.J[lane * kTheta + 21 + (lane - 20)] = 1.f;
     } else if (lane == 22) {
-      double dS[3][3], d2S[3][3][3];
+      real dS[3][3], d2S[3][3][3];
       sigma_derivs(th, dS, d2S);
       for (int e = 0; e < 3; ++e)
         for (int c = 0; c < 3; ++c) S.J[(22 + e) * kTheta + 23 + c] = dS[e][c];
-      double h[3][3] = {{0}};
+      real h[3][3] = {{0.f}};
       for (int e = 0; e < 3; ++e)
         for (int c = 0; c < 3; ++c)
           for (int d = 0; d < 3; ++d) h[c][d] += S.gnu[22 + e] * d2S[e][c][d];
       for (int c = 0; c < 3; ++c)
         for (int d = 0; d < 3; ++d) S.X[8 * 64 + c * 3 + d] = h[c][d];   // parked below
     } else if (lane == 25) {
-      const double r = sigm(th[26]);
-      S.J[25 * kTheta + 26] = r * (1.0 - r);
+      const real r = sigm(th[26]);
+      S.J[25 * kTheta + 26] = r * (1.f - r);
     }
     __syncwarp();
     // Sigma_s second-order chain term (parked by lane 22 past the KL scratch)
     if (lane < 9) S.Hth[(23 + lane / 3) * kTheta + 23 + lane % 3] += S.X[8 * 64 + lane];
     if (lane == 0) {
-      const double r = sigm(th[26]);
-      S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.0 - r) * (1.0 - 2.0 * r);
+      const real r = sigm(th[26]);
+      S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.f - r) * (1.f - 2.f * r);
     }
     __syncwarp();
     // gradient: J^T grad_nu over each column's rows
     if (lane < kTheta) {
       int rows[20];
       const int nr = col_rows(lane, rows);
-      double gsum = 0.0;
-      for (int k = 0; k < nr; ++k) gsum += S.J[rows[k] * kTheta + lane] * S.gnu[rows[k]];
+      real gsum = 0.f;
+      for (int k = 0; k < nr; ++k) gsum = fmaf(S.J[rows[k] * kTheta + lane], S.gnu[rows[k]], gsum);
       S.gth[lane] += gsum;
     }
     // X = H_nu J, only where J's column has support
@@ -451,8 +453,8 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       const int a = e / kTheta, c = e % kTheta;
       int rows[20];
       const int nr = col_rows(c, rows);
-      double x = 0.0;
-      for (int k = 0; k < nr; ++k) x += S.Hnu[a * kNu + rows[k]] * S.J[rows[k] * kTheta + c];
+      real x = 0.f;
+      for (int k = 0; k < nr; ++k) x = fmaf(S.Hnu[a * kNu + rows[k]], S.J[rows[k] * kTheta + c], x);
       S.X[e] = x;
     }
     __syncwarp();
@@ -463,14 +465,14 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       if (d < c) continue;
       int rows[20];
       const int nr = col_rows(c, rows);
-      double x = 0.0;
-      for (int k = 0; k < nr; ++k) x += S.J[rows[k] * kTheta + c] * S.X[rows[k] * kTheta + d];
+      real x = 0.f;
+      for (int k = 0; k < nr; ++k) x = fmaf(S.J[rows[k] * kTheta + c], S.X[rows[k] * kTheta + d], x);
       if (c <= 20 && d <= 20) {
         for (int k = 0; k < nr; ++k) {
           const int a = rows[k];
           if (a >= 20) break;
-          x += S.kw[a] * S.DL[a * kTheta + c] * S.DL[a * kTheta + d];
-          if (c == d) x += S.kw[a] * S.D2L[a * kTheta + c];
+          x = fmaf(S.kw[a] * S.DL[a * kTheta + c], S.DL[a * kTheta + d], x);
+          if (c == d) x = fmaf(S.kw[a], S.D2L[a * kTheta + c], x);
         }
       }
       S.Hth[c * kTheta + d] += x;
@@ -489,11 +491,11 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   if (kDerivs) {
     bool bad = false;
     for (int e = lane; e < kTheta; e += 32) {
-      grad_out[(size_t)j * kTheta + e] = S.gth[e];
+      grad_out[(size_t)j * kTheta + e] = (double)S.gth[e];
       bad |= !isfinite(S.gth[e]);
     }
     for (int e = lane; e < kTheta * kTheta; e += 32) {
-      hess_out[(size_t)j * kTheta * kTheta + e] = S.Hth[e];
+      hess_out[(size_t)j * kTheta * kTheta + e] = (double)S.Hth[e];
       bad |= !isfinite(S.Hth[e]);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(v.err, CELESTE_DERR_NONFINITE);
