@@ -35,7 +35,8 @@ __constant__ signed char kSelE[5][4] = {
 
 constexpr int kNu = 26;   // 20 flux moments (band b, kind e at 4b+e), u (2), Sigma_s (3), rho
 constexpr int kNuPad = 32;
-constexpr int kKlVals = 8 + 36 + 10 + 4;   // per colour component: grad, outer, prec, diag
+constexpr int kKlVals = 8 + 10 + 4;       // per colour component: grad, precision, diag
+constexpr int kKlSums = 64;                // per type: mean grad 8, centred outer 36, prec 10, diag 4
 
 __device__ __forceinline__ real sigm(real t) {
   return t >= 0.f ? 1.f / (1.f + expf(-t)) : expf(t) / (1.f + expf(t));
@@ -186,8 +187,6 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
         }
         for (int k = 0; k < 8; ++k) o[k] = gk[k];
         int t = 8;
-        for (int k = 0; k < 8; ++k)
-          for (int l = k; l < 8; ++l) o[t++] = gk[k] * gk[l];
         for (int k = 0; k < 4; ++k)
           for (int l = k; l < 4; ++l) o[t++] = (real)P[k][l];
         for (int k = 0; k < 4; ++k) o[t++] = 0.5f * (real)P[k][k] * cv[k];
@@ -213,13 +212,30 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     Bval[i] = -(S.kls[4 + i] + logf(se[i]));
   }
   if (kDerivs) {
-    // pi-weighted sums of the per-component pieces, per type (lanes over values)
+    // pi-weighted sums per type (S.X as scratch, kKlSums per type): the mean
+    // gradient, the precision block and the diagonal ...
     for (int e = lane; e < 2 * kKlVals; e += 32) {
       const int i = e / kKlVals, vv = e % kKlVals;
       real acc = 0.f;
       for (int j = 0; j < J; ++j)
         acc = fmaf(S.kw[i * kMaxColor + j], S.klc[(i * kMaxColor + j) * kKlVals + vv], acc);
-      S.X[i * 64 + vv] = acc / se[i];   // scratch
+      S.X[i * kKlSums + (vv < 8 ? vv : 36 + vv)] = acc / se[i];
+    }
+    __syncwarp();
+    // ... then the covariance of the gradients across components in centred
+    // form, sum_j pi_j (g_j - gbar)(g_j - gbar)^T, which does not cancel
+    for (int e = lane; e < 2 * 36; e += 32) {
+      const int i = e / 36;
+      int u = 0, rem = e % 36;
+      while (rem >= 8 - u) { rem -= 8 - u; ++u; }
+      const int w = u + rem;
+      const real gu = S.X[i * kKlSums + u], gw = S.X[i * kKlSums + w];
+      real acc = 0.f;
+      for (int j = 0; j < J; ++j) {
+        const real* gj = S.klc + (i * kMaxColor + j) * kKlVals;
+        acc = fmaf(S.kw[i * kMaxColor + j], (gj[u] - gu) * (gj[w] - gw), acc);
+      }
+      S.X[i * kKlSums + 8 + (e % 36)] = acc / se[i];
     }
   }
   __syncwarp();
@@ -254,7 +270,7 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
   };
   for (int e = lane; e < 2 * 100; e += 32) {
     const int i = e / 100, k = (e % 100) / 10, l = e % 10;
-    const real* pw = S.X + i * 64;            // pi-weighted: grad(8), outer(36), prec(10), diag(4)
+    const real* pw = S.X + i * kKlSums;       // grad(8), centred outer(36), prec(10), diag(4)
     const real R2 = (real)m->prior_r[i][1];
     const real rm = th[1 + 2 * i], rv = expf(th[2 + 2 * i]);
     // gradient of K_i = KL_r + B at local k
@@ -270,9 +286,9 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     } else {
       const int u = k - 2, w = l - 2;        // colour block 0..7
       const int lo = u < w ? u : w, hi = u < w ? w : u;
-      // sum_j pi_j (H_j - g_j g_j^T) + g g^T
+      // sum_j pi_j H_j - sum_j pi_j (g_j - gbar)(g_j - gbar)^T
       const int oi = lo * 8 - (lo * (lo - 1)) / 2 + (hi - lo);
-      h = -pw[8 + oi] + pw[lo] * pw[hi];
+      h = -pw[8 + oi];
       if (u < 4 && w < 4) {
         const int po = lo * 4 - (lo * (lo - 1)) / 2 + (hi - lo);
         h += pw[44 + po];

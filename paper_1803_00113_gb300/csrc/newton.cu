@@ -61,11 +61,12 @@ __device__ __forceinline__ double rcp64(double x) {
 }
 
 // Sturm count of T - sigma I in FP32 (pivot recurrence; scaled T, |T| <= 1).
-__device__ __forceinline__ int sturm32(const float* d, const float* e2, float sigma) {
+// d and e2 are register arrays (fully unrolled).
+__device__ __forceinline__ int sturm32(const float (&d)[N], const float (&e2)[N], float sigma) {
   int cnt = 0;
   float q = d[0] - sigma;
   cnt += q < 0.f;
-#pragma unroll 1
+#pragma unroll
   for (int i = 1; i < N; ++i) {
     const float qp = q == 0.f ? 1e-30f : q;
     q = (d[i] - sigma) - __fdividef(e2[i - 1], qp);
@@ -77,13 +78,13 @@ __device__ __forceinline__ int sturm32(const float* d, const float* e2, float si
 // Sturm count of T - sigma I in FP64 without divisions: sign changes of the
 // characteristic-polynomial sequence p_0 = 1, p_1 = d_0 - sigma,
 // p_{i+1} = (d_i - sigma) p_i - e_{i-1}^2 p_{i-1} (scaled T keeps |p_i| <= 3^27).
-__device__ __forceinline__ int sturm64(const double* d, const double* e, double sigma) {
+__device__ __forceinline__ int sturm64(const double (&d)[N], const double (&e2)[N], double sigma) {
   double pm = 1.0, p = d[0] - sigma;
   int cnt = (p < 0.0);
   bool neg = p <= 0.0;
-#pragma unroll 1
+#pragma unroll
   for (int i = 1; i < N; ++i) {
-    const double pn = (d[i] - sigma) * p - e[i - 1] * e[i - 1] * pm;
+    const double pn = fma(d[i] - sigma, p, -e2[i - 1] * pm);
     const bool nn = pn < 0.0 || (pn == 0.0 && !neg);
     cnt += (nn != neg);
     neg = nn;
@@ -206,7 +207,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
           r = rsqrt(nrm2);
         }
         const double alpha = -copysign(nrm2 * r, x0);
-        const double bt = 1.0 / fma(-x0, alpha, nrm2);
+        const double bt = rcp64(fma(-x0, alpha, nrm2));
         if (lane < m) S.B[(k + 1 + lane) * N + k] = xv - (lane == 0 ? alpha : 0.0);
         if (lane == 0) {
           S.beta[k] = bt;
@@ -284,10 +285,16 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     b = fmax(b, d[i] + r);
   }
   {
+    float rd[N], re2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      rd[i] = S.df[i];
+      re2[i] = S.e2f[i];
+    }
     float fa = (float)a - 1e-6f, fb = (float)b + 1e-6f;
     for (int round = 0; round < 5; ++round) {
       const float sig = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
-      const bool hit = lane < 31 && sturm32(S.df, S.e2f, sig) >= 1;
+      const bool hit = lane < 31 && sturm32(rd, re2, sig) >= 1;
       const unsigned mask = __ballot_sync(0xffffffffu, hit);
       const int t = mask ? __ffs(mask) - 1 : 31;
       const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
@@ -299,15 +306,23 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     a = fmax(a - 1e-6, (double)fa - 1e-5);
     b = fmin(b + 1e-6, (double)fb + 1e-5);
   }
-  for (int round = 0; round < 4; ++round) {
-    const double sig = a + (b - a) * (double)(lane + 1) * (1.0 / 32.0);
-    const bool hit = lane < 31 && sturm64(d, e, sig) >= 1;
+  {
+    double rd[N], re2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      rd[i] = d[i];
+      re2[i] = e[i] * e[i];
+    }
+    for (int round = 0; round < 4; ++round) {
+      const double sig = a + (b - a) * (double)(lane + 1) * (1.0 / 32.0);
+      const bool hit = lane < 31 && sturm64(rd, re2, sig) >= 1;
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
     const int t = mask ? __ffs(mask) - 1 : 31;
     const double na = t == 0 ? a : a + (b - a) * (double)t * (1.0 / 32.0);
     const double nb = t == 31 ? b : a + (b - a) * (double)(t + 1) * (1.0 / 32.0);
     a = na;
     b = nb;
+    }
   }
   const double lmin = 0.5 * (a + b);    // scaled
   // ---- multiplier (scaled units: l / scale); |y| is scale-invariant
@@ -349,7 +364,9 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
         const double n2 = ldl_solve(d, e, gs, l, S.y, &q);
         const double ny = sqrt(n2);
         if (n2 <= D2) lb = l; else la = l;
-        if (fabs(ny - Delta) <= 1e-13 * Delta) break;
+        // stop on the norm, or when the bracket is down to rounding (close
+        // to the pole |y| is too steep in l for the norm test)
+        if (fabs(ny - Delta) <= 1e-12 * Delta || lb - la <= 4e-16 * lb) break;
         double ln = l + (ny - Delta) / Delta * n2 / q;
         if (!(ln > la && ln < lb)) ln = 0.5 * (la + lb);
         if (ln == l) break;
@@ -411,7 +428,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   return true;
 }
 
-__global__ void __launch_bounds__(kTrThreads) tr_subproblem_kernel(int n, const double* g,
+__global__ void __launch_bounds__(kTrThreads, 4) tr_subproblem_kernel(int n, const double* g,
                                                                   const double* H,
                                                                   const double* delta, double* p,
                                                                   double* pred) {
@@ -426,7 +443,7 @@ __global__ void __launch_bounds__(kTrThreads) tr_subproblem_kernel(int n, const 
 }
 
 // Step of every active slot: converged sources leave the active set.
-__global__ void __launch_bounds__(kTrThreads) tr_step_kernel(PlanView v, const double* delta,
+__global__ void __launch_bounds__(kTrThreads, 4) tr_step_kernel(PlanView v, const double* delta,
                                                             int32_t* status) {
   extern __shared__ double smd[];
   TrSmem& S = *reinterpret_cast<TrSmem*>(smd);
