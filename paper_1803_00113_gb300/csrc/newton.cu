@@ -51,13 +51,11 @@ struct TrSmem {
   int skip[32];                    // per Householder step: column already reduced
 };
 
-// 1 / x in FP64 from an FP32 seed and two Newton steps (|x| within FP32
-// range; callers pass scaled values).
+// 1 / x in FP64 from an FP32 seed and one Newton step (relative error
+// ~1e-14; |x| within FP32 range: callers pass scaled values).
 __device__ __forceinline__ double rcp64(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = r * fma(-x, r, 2.0);
-  r = r * fma(-x, r, 2.0);
-  return r;
+  const double r = (double)__frcp_rn((float)x);
+  return r * fma(-x, r, 2.0);
 }
 
 // Sturm count of T - sigma I in FP32 (pivot recurrence; scaled T, |T| <= 1).
@@ -201,8 +199,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
         double r;
         if (nrm2 > 1e-30 && nrm2 < 1e30) {
           r = (double)rsqrtf((float)nrm2);                     // FP32 seed, then
-          r = r * fma(-0.5 * nrm2 * r, r, 1.5);                // two Newton steps
-          r = r * fma(-0.5 * nrm2 * r, r, 1.5);
+          r = r * fma(-0.5 * nrm2 * r, r, 1.5);                // one Newton step
         } else {
           r = rsqrt(nrm2);
         }
@@ -256,14 +253,21 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   }
   __syncwarp();
   apply_q(S, S.gh, true, lane);
-  // ---- scale: |T / scale| <= 1 (Gershgorin)
-  double scale = 0.0, gn2 = 0.0;
-  for (int i = 0; i < N; ++i) {
-    scale = fmax(scale, fabs(S.d[i]) + fabs(S.e[i]) + (i ? fabs(S.e[i - 1]) : 0.0));
-    gn2 = fma(S.gh[i], S.gh[i], gn2);
+  // ---- scale: |T / scale| <= 1 (Gershgorin), bookkeeping in FP32
+  float rowf = 0.f, g2f = 0.f;
+  if (lane < N) {
+    rowf = fabsf((float)S.d[lane]) + fabsf((float)S.e[lane]) + (lane ? fabsf((float)S.e[lane - 1]) : 0.f);
+    const float gf = (float)S.gh[lane];
+    g2f = gf * gf;
   }
-  scale = fmax(scale, 1e-300);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rowf = fmaxf(rowf, __shfl_xor_sync(0xffffffffu, rowf, o));
+    g2f += __shfl_xor_sync(0xffffffffu, g2f, o);
+  }
+  const double scale = (double)fmaxf(rowf, 1e-30f);
   const double inv = 1.0 / scale;
+  const float gnorm_s = sqrtf(g2f) * (float)inv;   // |g| / scale
   if (lane < N) {
     S.ds[lane] = S.d[lane] * inv;
     S.es[lane] = S.e[lane] * inv;
@@ -277,13 +281,19 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   const double* d = S.ds;
   const double* e = S.es;
   const double* gs = S.gs;
-  // ---- lambda_min of the scaled matrix
-  double a = 1.0, b = -1.0;
-  for (int i = 0; i < N; ++i) {
-    const double r = fabs(e[i]) + (i ? fabs(e[i - 1]) : 0.0);
-    a = fmin(a, d[i] - r);
-    b = fmax(b, d[i] + r);
+  // ---- lambda_min of the scaled matrix: Gershgorin bracket (FP32)
+  float af = 1.f, bf = -1.f;
+  if (lane < N) {
+    const float r = fabsf(S.ef[lane]) + (lane ? fabsf(S.ef[lane - 1]) : 0.f);
+    af = S.df[lane] - r;
+    bf = S.df[lane] + r;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    af = fminf(af, __shfl_xor_sync(0xffffffffu, af, o));
+    bf = fmaxf(bf, __shfl_xor_sync(0xffffffffu, bf, o));
+  }
+  double a = (double)af, b = (double)bf;
   {
     float rd[N], re2[N];
 #pragma unroll
@@ -313,7 +323,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
       rd[i] = d[i];
       re2[i] = e[i] * e[i];
     }
-    for (int round = 0; round < 4; ++round) {
+    for (int round = 0; round < 3; ++round) {
       const double sig = a + (b - a) * (double)(lane + 1) * (1.0 / 32.0);
       const bool hit = lane < 31 && sturm64(rd, re2, sig) >= 1;
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
@@ -324,7 +334,9 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     b = nb;
     }
   }
-  const double lmin = 0.5 * (a + b);    // scaled
+  // a lower bound of lambda_min within ~1e-9 of it (scaled): T + l I is
+  // positive definite for every l > -lmin
+  const double lmin = a;
   // ---- multiplier (scaled units: l / scale); |y| is scale-invariant
   const double D2 = Delta * Delta;
   bool done = false, hard = false;
@@ -336,7 +348,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     const double lo = fmax(0.0, -lmin);
     const double eps = 1e-12;
     double la = lo + eps;
-    double lb = lo + sqrt(gn2) * inv / Delta + eps;
+    double lb = lo + (double)gnorm_s / Delta * (1.0 + 1e-6) + eps;
     // FP32 multisection for a starting point; in the first round lane 31
     // probes la itself (the hard-case test)
     float fa = (float)la, fb = (float)lb;
@@ -410,18 +422,18 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     if (lane < N) S.y[lane] = fma(tau, S.w[lane], S.y[lane]);
     __syncwarp();
   }
-  // predicted gain: y.Q^T g - y.T.y / 2 (unscaled T)
-  if (lane == 0) {
-    double gy = 0.0, yty = 0.0;
-    for (int i = 0; i < N; ++i) {
-      const double yi = S.y[i];
-      gy = fma(yi, S.gh[i], gy);
-      double ty = S.d[i] * yi;
-      if (i > 0) ty = fma(S.e[i - 1], S.y[i - 1], ty);
-      if (i < N - 1) ty = fma(S.e[i], S.y[i + 1], ty);
-      yty = fma(yi, ty, yty);
+  // predicted gain: y.Q^T g - y.T.y / 2 (unscaled T), one row per lane
+  {
+    double term = 0.0;
+    if (lane < N) {
+      const double yi = S.y[lane];
+      double ty = S.d[lane] * yi;
+      if (lane > 0) ty = fma(S.e[lane - 1], S.y[lane - 1], ty);
+      if (lane < N - 1) ty = fma(S.e[lane], S.y[lane + 1], ty);
+      term = yi * fma(-0.5, ty, S.gh[lane]);
     }
-    S.red[0] = gy - 0.5 * yty;
+    term = warp_sum_d(term);
+    if (lane == 0) S.red[0] = term;
   }
   __syncwarp();
   apply_q(S, S.y, false, lane);
