@@ -201,6 +201,13 @@ int64_t celeste_plan_visits(const celeste_plan* plan);
 int celeste_elbo_grad_hess(celeste_ctx* ctx, const celeste_plan* plan,
                            double* elbo, double* elbo_rel, double* grad, double* hess);
 
+/* Value and gradient only (the gradient-only mode): the pixel pass keeps 12
+ * sums per tile instead of 64, about a third of the work of
+ * celeste_elbo_grad_hess (Sec. 4.3 compares the two costs).  Outputs as in
+ * celeste_elbo_grad_hess; elbo and elbo_rel may be NULL. */
+int celeste_elbo_grad(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, double* elbo_rel,
+                      double* grad);
+
 /* Value only (no derivatives): elbo[n] and elbo_rel[n] (either may be NULL). */
 int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, double* elbo_rel);
 

@@ -81,6 +81,7 @@ def lib():
         "celeste_plan_visits": (I64, [P]),
         "celeste_elbo_grad_hess": (ctypes.c_int, [P, P, P, P, P, P]),
         "celeste_elbo": (ctypes.c_int, [P, P, P, P]),
+        "celeste_elbo_grad": (ctypes.c_int, [P, P, P, P, P]),
         "celeste_newton_step": (ctypes.c_int, [P, P, P, P, P]),
         "celeste_tr_subproblem": (ctypes.c_int, [P, I32, P, P, P, P, P]),
         "celeste_render": (ctypes.c_int, [P, P, P, P]),
@@ -103,7 +104,7 @@ def exported_symbols():
     return ["celeste_create", "celeste_destroy", "celeste_synchronize", "celeste_launch_count",
             "celeste_profile_enable", "celeste_profile_read",
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
-            "celeste_elbo_grad_hess", "celeste_elbo", "celeste_newton_step",
+            "celeste_elbo_grad_hess", "celeste_elbo", "celeste_elbo_grad", "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
             "celeste_color_sources", "celeste_elbo_grad_hess_noalloc"]
 
@@ -313,6 +314,20 @@ def elbo_grad_hess(plan: Plan, out=None):
     e, er, g, H = out
     _check(lib().celeste_elbo_grad_hess(plan.ctx.handle, plan.handle, _ptr(e), _ptr(er), _ptr(g),
                                         _ptr(H)), "celeste_elbo_grad_hess")
+    return out
+
+
+def elbo_grad(plan: Plan, out=None):
+    """(elbo, elbo_rel, grad [n, 27]) as float64 device tensors (gradient-only mode)."""
+    dev = plan.ctx.device
+    n = plan.n
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float64, device=dev),
+               torch.empty(n, dtype=torch.float64, device=dev),
+               torch.empty(n, N_THETA, dtype=torch.float64, device=dev))
+    e, er, g = out
+    _check(lib().celeste_elbo_grad(plan.ctx.handle, plan.handle, _ptr(e), _ptr(er), _ptr(g)),
+           "celeste_elbo_grad")
     return out
 
 

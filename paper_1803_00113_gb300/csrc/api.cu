@@ -475,6 +475,22 @@ int celeste_elbo_grad_hess(celeste_ctx* c, const celeste_plan* pc, double* elbo,
   return to_status(launch_epilogue(L, p->v, c->d_model, elbo, elbo_rel, grad, hess));
 }
 
+int celeste_elbo_grad(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel,
+                      double* grad) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c) return CELESTE_EINVAL;
+  if (p->v.n == 0) return CELESTE_OK;
+  if (!grad) return CELESTE_EINVAL;
+  Launch L = make_launch(c, p);
+  CK(cudaMemsetAsync(p->v.active, 1, p->v.n > 0 ? p->v.n : 1, c->stream));
+  int rc = run_setup(c, p, 0, p->v.n_pairs, false);
+  if (rc) return rc;
+  c->launches += 3;
+  CK(launch_background(L, p->v));
+  CK(launch_pixels_grad(L, p->v));
+  return to_status(launch_epilogue_grad(L, p->v, c->d_model, elbo, elbo_rel, grad));
+}
+
 int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel) {
   celeste_plan* p = const_cast<celeste_plan*>(pc);
   if (!c || !p || p->ctx != c) return CELESTE_EINVAL;

@@ -148,9 +148,10 @@ __device__ void sigma_derivs(const real* th, real dS[3][3], real d2S[3][3][3]) {
   d2S[1][2][2] = -Qtt * S2;
 }
 
-// KL_s: value into S.kls[0]; with kDerivs, gradient and Hessian are
-// ADDED (with a minus sign, since L = ... - KL) into S.gth and S.Hth.
-template <bool kDerivs>
+// KL_s: value into S.kls[0]; for kMode >= 1 the gradient and for kMode == 2
+// also the Hessian are ADDED (with a minus sign, since L = ... - KL) into
+// S.gth and S.Hth.
+template <int kMode>
 __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane) {
   const real a = sigm(th[0]);
   const real wq = a * (1.f - a);
@@ -178,7 +179,7 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
       }
       const real K = 0.5f * (tr + quad - 4.f + (real)m->color_logdet[i][j] - slv);
       S.klj[lane] = (real)m->log_color_w[i][j] - K;
-      if (kDerivs) {
+      if (kMode >= 1) {
         real* o = S.klc + lane * kKlVals;
         real gk[8];
         for (int k = 0; k < 4; ++k) {
@@ -211,7 +212,7 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     for (int j = 0; j < J; ++j) se[i] += S.kw[i * kMaxColor + j];
     Bval[i] = -(S.kls[4 + i] + logf(se[i]));
   }
-  if (kDerivs) {
+  if (kMode >= 1) {
     // pi-weighted sums per type (S.X as scratch, kKlSums per type): the mean
     // gradient, the precision block and the diagonal ...
     for (int e = lane; e < 2 * kKlVals; e += 32) {
@@ -224,7 +225,7 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     __syncwarp();
     // ... then the covariance of the gradients across components in centred
     // form, sum_j pi_j (g_j - gbar)(g_j - gbar)^T, which does not cancel
-    for (int e = lane; e < 2 * 36; e += 32) {
+    for (int e = lane; e < (kMode == 2 ? 2 * 36 : 0); e += 32) {
       const int i = e / 36;
       int u = 0, rem = e % 36;
       while (rem >= 8 - u) { rem -= 8 - u; ++u; }
@@ -262,13 +263,15 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     S.kls[0] = v;
   }
   __syncwarp();
-  if (!kDerivs) return;
+  if (kMode == 0) return;
   // per type i, local coordinates 0 r-mean, 1 log r-var, 2..5 colour means,
   // 6..9 log colour vars; theta index of local k:
   auto tidx = [](int i, int k) {
     return k == 0 ? 1 + 2 * i : (k == 1 ? 2 + 2 * i : (k < 6 ? 5 + 4 * i + (k - 2) : 13 + 4 * i + (k - 6)));
   };
-  for (int e = lane; e < 2 * 100; e += 32) {
+  // gradient-only mode visits the (i, k, l = 0) entries only
+  for (int e0 = lane; e0 < (kMode == 2 ? 200 : 20); e0 += 32) {
+    const int e = kMode == 2 ? e0 : (e0 / 10) * 100 + (e0 % 10) * 10;
     const int i = e / 100, k = (e % 100) / 10, l = e % 10;
     const real* pw = S.X + i * kKlSums;       // grad(8), centred outer(36), prec(10), diag(4)
     const real R2 = (real)m->prior_r[i][1];
@@ -297,13 +300,15 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
       }
     }
     const real qi = i ? a : 1.f - a;
-    S.Hth[tidx(i, k) * kTheta + tidx(i, l)] -= qi * h;
+    if (kMode == 2) S.Hth[tidx(i, k) * kTheta + tidx(i, l)] -= qi * h;
     if (l == 0) {
       const real dq = i ? wq : -wq;
       const real g = gK(k);
       S.gth[tidx(i, k)] -= qi * g;
-      S.Hth[tidx(i, k) * kTheta + 0] -= dq * g;
-      S.Hth[0 * kTheta + tidx(i, k)] -= dq * g;
+      if (kMode == 2) {
+        S.Hth[tidx(i, k) * kTheta + 0] -= dq * g;
+        S.Hth[0 * kTheta + tidx(i, k)] -= dq * g;
+      }
     }
   }
   __syncwarp();
@@ -311,23 +316,25 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     const real la = (real)m->logit_prior_a;
     const real d2q = wq * (1.f - 2.f * a);
     S.gth[0] -= wq * (th[0] - la) + wq * (S.kls[3] - S.kls[2]);
-    S.Hth[0] -= wq * ((1.f - 2.f * a) * (th[0] - la) + 1.f) + d2q * (S.kls[3] - S.kls[2]);
+    if (kMode == 2)
+      S.Hth[0] -= wq * ((1.f - 2.f * a) * (th[0] - la) + 1.f) + d2q * (S.kls[3] - S.kls[2]);
     const real lr = th[24], E1 = (real)m->e_radius[0], E2 = (real)m->e_radius[1];
     S.gth[24] -= 1.f + (lr - E1) / E2;
-    S.Hth[24 * kTheta + 24] -= 1.f / E2;
+    if (kMode == 2) S.Hth[24 * kTheta + 24] -= 1.f / E2;
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
       const real b1 = (real)(which ? m->e_profile[0] : m->e_axis[0]);
       const real b2 = (real)(which ? m->e_profile[1] : m->e_axis[1]);
       const real sg = sigm(th[t]);
       S.gth[t] -= -(b1 - 1.f) * (1.f - sg) + (b2 - 1.f) * sg;
-      S.Hth[t * kTheta + t] -= (b1 + b2 - 2.f) * sg * (1.f - sg);
+      if (kMode == 2) S.Hth[t * kTheta + t] -= (b1 + b2 - 2.f) * sg * (1.f - sg);
     }
   }
   __syncwarp();
 }
 
-template <bool kDerivs>
+// kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian.
+template <int kMode>
 __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, double* elbo,
                                 double* elbo_rel, double* grad_out, double* hess_out,
                                 int use_trial) {
@@ -342,16 +349,18 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   const real* th = S.th;
 
   double vrel = 0.0, vbase = 0.0;
-  if (kDerivs) {
+  if (kMode >= 1) {
     for (int e = lane; e < kNuPad; e += 32) S.gnu[e] = 0.f;
-    for (int e = lane; e < kNu * kNu; e += 32) S.Hnu[e] = 0.f;
     for (int e = lane; e < kNuPad; e += 32) S.gth[e] = 0.f;
+  }
+  if (kMode == 2) {
+    for (int e = lane; e < kNu * kNu; e += 32) S.Hnu[e] = 0.f;
     for (int e = lane; e < kTheta * kTheta; e += 32) S.Hth[e] = 0.f;
   }
   __syncwarp();
   for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
     const PairInfo pi = v.pairs[pp];
-    if (!kDerivs) {
+    if (kMode == 0) {
       double r = 0.0, b = 0.0;
       for (int it = pi.item_begin + lane; it < pi.item_end; it += 32) {
         r += (double)v.vpartials[2 * (size_t)it];
@@ -362,9 +371,11 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       continue;
     }
     double w0 = 0.0, w1 = 0.0;
-    for (int it = pi.item_begin; it < pi.item_end; ++it) {
-      w0 += (double)v.partials[(size_t)it * kAcc + lane];
-      w1 += (double)v.partials[(size_t)it * kAcc + 32 + lane];
+    if (kMode == 2 || lane < kGradAcc) {
+      for (int it = pi.item_begin; it < pi.item_end; ++it) {
+        w0 += (double)v.partials[(size_t)it * kAcc + lane];
+        if (kMode == 2) w1 += (double)v.partials[(size_t)it * kAcc + 32 + lane];
+      }
     }
     S.W[lane] = w0;
     S.W[lane + 32] = w1;
@@ -398,7 +409,7 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       for (int k = lo(lane); k < hi(lane); ++k) gl += S.T[k * 10 + lane] * (float)S.W[2 + k];
       S.gnu[nu_of(lane)] += gl;
     }
-    for (int e = lane; e < 55; e += 32) {
+    for (int e = lane; e < (kMode == 2 ? 55 : 0); e += 32) {
       int a = 0, rem = e;
       while (rem >= 10 - a) { rem -= 10 - a; ++a; }
       const int c = a + rem;
@@ -419,9 +430,9 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
     __syncwarp();
   }
 
-  kl_terms<kDerivs>(th, model, S, lane);
+  kl_terms<kMode>(th, model, S, lane);
   const double kl = (double)S.kls[0];
-  if (kDerivs) {
+  if (kMode >= 1) {
     // Jacobian rows: flux moments (lanes 0..19), u, Sigma_s, rho
     for (int e = lane; e < kNu * kTheta; e += 32) S.J[e] = 0.f;
     __syncwarp();
@@ -449,11 +460,13 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       S.J[25 * kTheta + 26] = r * (1.f - r);
     }
     __syncwarp();
-    // Sigma_s second-order chain term (parked by lane 22 past the KL scratch)
-    if (lane < 9) S.Hth[(23 + lane / 3) * kTheta + 23 + lane % 3] += S.X[8 * 64 + lane];
-    if (lane == 0) {
-      const real r = sigm(th[26]);
-      S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.f - r) * (1.f - 2.f * r);
+    if (kMode == 2) {
+      // Sigma_s second-order chain term (parked by lane 22 past the KL scratch)
+      if (lane < 9) S.Hth[(23 + lane / 3) * kTheta + 23 + lane % 3] += S.X[8 * 64 + lane];
+      if (lane == 0) {
+        const real r = sigm(th[26]);
+        S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.f - r) * (1.f - 2.f * r);
+      }
     }
     __syncwarp();
     // gradient: J^T grad_nu over each column's rows
@@ -465,7 +478,7 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       S.gth[lane] += gsum;
     }
     // X = H_nu J, only where J's column has support
-    for (int e = lane; e < kNu * kTheta; e += 32) {
+    for (int e = lane; e < (kMode == 2 ? kNu * kTheta : 0); e += 32) {
       const int a = e / kTheta, c = e % kTheta;
       int rows[20];
       const int nr = col_rows(c, rows);
@@ -476,7 +489,7 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
     __syncwarp();
     // Hth += J^T X (upper triangle, mirrored), plus the flux-moment
     // second-order term sum_a kw_a (dl dl^T + diag d2l)
-    for (int e = lane; e < kTheta * kTheta; e += 32) {
+    for (int e = lane; e < (kMode == 2 ? kTheta * kTheta : 0); e += 32) {
       const int c = e / kTheta, d = e % kTheta;
       if (d < c) continue;
       int rows[20];
@@ -504,13 +517,13 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
     if (elbo_rel) elbo_rel[j] = Lrel;
     if (!isfinite(Lfull)) set_error(v.err, CELESTE_DERR_NONFINITE);
   }
-  if (kDerivs) {
+  if (kMode >= 1) {
     bool bad = false;
     for (int e = lane; e < kTheta; e += 32) {
       grad_out[(size_t)j * kTheta + e] = (double)S.gth[e];
       bad |= !isfinite(S.gth[e]);
     }
-    for (int e = lane; e < kTheta * kTheta; e += 32) {
+    for (int e = lane; e < (kMode == 2 ? kTheta * kTheta : 0); e += 32) {
       hess_out[(size_t)j * kTheta * kTheta + e] = (double)S.Hth[e];
       bad |= !isfinite(S.Hth[e]);
     }
@@ -518,11 +531,11 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   }
 }
 
-template <bool kDerivs>
+template <int kMode>
 static void set_smem_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(epilogue_kernel<kDerivs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(epilogue_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(EpiSmem));
     done = true;
   }
@@ -531,19 +544,27 @@ static void set_smem_attr() {
 cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* model,
                             double* elbo, double* elbo_rel, double* grad, double* hess) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<true>();
-  epilogue_kernel<true><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
-                                                                 hess, 0);
+  set_smem_attr<2>();
+  epilogue_kernel<2><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
+                                                              hess, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const ModelDev* model,
+                                 double* elbo, double* elbo_rel, double* grad) {
+  if (v.n == 0) return cudaSuccess;
+  set_smem_attr<1>();
+  epilogue_kernel<1><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
+                                                              nullptr, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
                                   double* elbo, double* elbo_rel, bool use_trial) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<false>();
-  epilogue_kernel<false><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel,
-                                                                  nullptr, nullptr,
-                                                                  use_trial ? 1 : 0);
+  set_smem_attr<0>();
+  epilogue_kernel<0><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, nullptr,
+                                                              nullptr, use_trial ? 1 : 0);
   return cudaGetLastError();
 }
 

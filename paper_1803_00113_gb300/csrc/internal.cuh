@@ -37,6 +37,7 @@ enum : int { C_MX = 0, C_MY, C_P11, C_P12, C_P22, C_LW, C_TAU };
 // (cM, cM) entries, which vanish identically.
 constexpr int kW = 10;
 constexpr int kAcc = 64;
+constexpr int kGradAcc = 12;   // gradient-only items: value_rel, value_base, grad[10]
 __host__ __device__ constexpr int hidx(int j, int k) {
   // packed upper triangle (row-major, j <= k) of the 10 x 10 Hessian, minus
   // the entries (2,2), (2,3) and (3,3), which are never stored
@@ -129,6 +130,7 @@ cudaError_t launch_setup(const Launch& L, const PlanView& v, const ModelDev* mod
 // pixel.cu
 cudaError_t launch_background(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v);
+cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_value(const Launch& L, const PlanView& v);
 cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, float* V_out,
                           const celeste_patch* patches);
@@ -137,6 +139,8 @@ cudaError_t launch_background_out(const Launch& L, const PlanView& v, float* bgE
 // epilogue.cu
 cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* model,
                             double* elbo, double* elbo_rel, double* grad, double* hess);
+cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const ModelDev* model,
+                                 double* elbo, double* elbo_rel, double* grad);
 cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
                                   double* elbo, double* elbo_rel, bool use_trial);
 // newton.cu

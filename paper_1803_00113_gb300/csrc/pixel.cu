@@ -264,6 +264,92 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
   }
 }
 
+// Gradient-only sums of one galaxy profile: value, d mu, and the
+// tau-weighted second order for dG (the heat equation again).
+struct GalSums1 {
+  float s0, s1x, s1y, t2xx, t2xy, t2yy;
+};
+
+__device__ __forceinline__ void gal_accumulate1(const float* __restrict__ c, float px, float py,
+                                                GalSums1& g) {
+  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
+  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const float y1 = fmaf(P11, dx, P12 * dy);
+  const float y2 = fmaf(P12, dx, P22 * dy);
+  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
+  const float pt = phi * c[C_TAU];
+  g.s0 += phi;
+  g.s1x = fmaf(phi, y1, g.s1x);
+  g.s1y = fmaf(phi, y2, g.s1y);
+  g.t2xx = fmaf(pt, fmaf(y1, y1, -P11), g.t2xx);
+  g.t2xy = fmaf(pt, fmaf(y1, y2, -P12), g.t2xy);
+  g.t2yy = fmaf(pt, fmaf(y2, y2, -P22), g.t2yy);
+}
+
+// One pixel, value and gradient only (the adjoint of the pixel term through
+// E_s and M_s onto the per-image natural coordinates): 12 accumulators.
+__device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne, int nd,
+                                           float px, float py, float x, float2 bg,
+                                           float* __restrict__ acc) {
+  float F1 = 0.f, sx = 0.f, sy = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPsf; ++k) {
+    const float* c = rec + kHdr + k * kCompF;
+    const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
+    const float dx = px - c[C_MX], dy = py - c[C_MY];
+    const float y1 = fmaf(P11, dx, P12 * dy);
+    const float y2 = fmaf(P12, dx, P22 * dy);
+    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
+    F1 += phi;
+    sx = fmaf(phi, y1, sx);
+    sy = fmaf(phi, y2, sy);
+  }
+  GalSums1 ge = {}, gd = {};
+  const int per = ne + nd;
+  for (int k = 0; k < kPsf; ++k) {
+    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
+    for (int j = 0; j < ne; ++j) gal_accumulate1(base + j * kCompF, px, py, ge);
+    for (int j = 0; j < nd; ++j) gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
+  }
+  const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
+#define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
+  const float F0 = MIX(s0);
+  float d0[6];
+  d0[0] = MIX(s1x);
+  d0[1] = MIX(s1y);
+  d0[2] = 0.5f * MIX(t2xx);
+  d0[3] = MIX(t2xy);
+  d0[4] = 0.5f * MIX(t2yy);
+  d0[5] = ge.s0 - gd.s0;
+#undef MIX
+  const float cE0 = rec[H_CE0], cE1 = rec[H_CE1], cM0 = rec[H_CM0], cM1 = rec[H_CM1];
+  float Es, Vs;
+  own_moments(rec, F0, F1, Es, Vs);
+  const float bgE = bg.x, bgV = bg.y;
+  const float E = bgE + Es, V = bgV + Vs;
+  const float r = __frcp_rn(E);
+  const float rb = __frcp_rn(bgE);
+  const float xr2 = x * r * r;
+  const float TE = fmaf(x - E, r, xr2 * r * V);
+  const float TV = -0.5f * xr2;
+  const float tE = fmaf(-2.f * Es, TV, TE);
+  const float tM = TV;
+  acc[0] += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bgV * rb * rb, -Es);
+  acc[1] += fmaf(x, __logf(bgE) - 0.5f * bgV * rb * rb, -bgE);
+  const float m0 = 2.f * cM0 * F0, m1 = 2.f * cM1 * F1;
+  acc[2] = fmaf(tE, F0, acc[2]);
+  acc[3] = fmaf(tE, F1, acc[3]);
+  acc[4] = fmaf(tM, F0 * F0, acc[4]);
+  acc[5] = fmaf(tM, F1 * F1, acc[5]);
+  const float a0 = fmaf(cE0, d0[0], cE1 * sx), a1 = fmaf(cE0, d0[1], cE1 * sy);
+  const float b0 = fmaf(m0, d0[0], m1 * sx), b1 = fmaf(m0, d0[1], m1 * sy);
+  acc[6] = fmaf(tE, a0, fmaf(tM, b0, acc[6]));
+  acc[7] = fmaf(tE, a1, fmaf(tM, b1, acc[7]));
+  const float cg = fmaf(tE, cE0, tM * m0);
+#pragma unroll
+  for (int g = 2; g < 6; ++g) acc[6 + g] = fmaf(cg, d0[g], acc[6 + g]);
+}
+
 // Writes the 64 warp-reduced sums of one item (lane a holds sums a, a + 32).
 __device__ __forceinline__ void reduce_store(float* __restrict__ acc, float* __restrict__ out,
                                              int lane) {
@@ -307,6 +393,40 @@ __global__ void __launch_bounds__(128) derivs_kernel(PlanView v, int ne, int nd)
       pixel_derivs(rec, ne, nd, (float)qx, (float)qy, x, bg, acc);
     }
     reduce_store(acc, v.partials + (size_t)it * kAcc, lane);
+  }
+}
+
+__global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (!v.active[pi.slot]) continue;
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    float acc[kGradAcc];
+#pragma unroll
+    for (int a = 0; a < kGradAcc; ++a) acc[a] = 0.f;
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
+      const float2 bg = v.bg[pi.bg_base + q];
+      pixel_grad(rec, ne, nd, (float)qx, (float)qy, x, bg, acc);
+    }
+#pragma unroll
+    for (int a = 0; a < kGradAcc; ++a) acc[a] = warp_sum(acc[a]);
+    float* out = v.partials + (size_t)it * kAcc;
+#pragma unroll
+    for (int a = 0; a < kGradAcc; ++a)
+      if (a == lane) out[a] = acc[a];
   }
 }
 
@@ -459,6 +579,13 @@ cudaError_t launch_background(const Launch& L, const PlanView& v) {
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
   derivs_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
+  if (v.n_items == 0) return cudaSuccess;
+  grad_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
