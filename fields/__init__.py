@@ -354,11 +354,23 @@ class _Builder:
         # photon counts: Poisson draws around sky + the simplified truth render
         # (sky >= 50 counts everywhere, so a rounded normal with variance
         # lambda stands in for the Poisson draw; this keeps large batches fast)
+        lam = np.concatenate(self.pix)
+        off = 0
         for n, d in enumerate(self.img):
-            lam = self.sky_at(n) + self.pix[n].reshape(d["h"], d["stride"])[:, :d["w"]]
-            z = rng.standard_normal(lam.shape, dtype=np.float32)
-            counts = np.maximum(np.rint(lam + np.sqrt(lam) * z), 0.0).astype(np.float32)
-            self.pix[n] = counts.ravel()
+            size = d["h"] * d["stride"]
+            if d["sky_ny"] == 1 and d["sky_nx"] == 1:
+                lam[off:off + size] += float(self.sky[n][0])
+            else:
+                lam[off:off + size] += self.sky_at(n).ravel()
+            off += size
+        z = rng.standard_normal(lam.size, dtype=np.float32)
+        z *= np.sqrt(lam.astype(np.float32))
+        counts = np.maximum(np.rint(lam + z), 0.0).astype(np.float32)
+        off = 0
+        for n, d in enumerate(self.img):
+            size = d["h"] * d["stride"]
+            self.pix[n] = counts[off:off + size]
+            off += size
         pp = np.zeros(len(self.patches) + 1, dtype=np.int32)
         flat = []
         for s, pl in enumerate(self.patches):
@@ -372,7 +384,7 @@ class _Builder:
         I = self.img
         return Problem(
             model=self.model,
-            pixels=np.concatenate(self.pix).astype(np.float32),
+            pixels=counts,
             sky=np.concatenate(self.sky).astype(np.float32),
             img_band=np.array([d["band"] for d in I], dtype=np.int32),
             img_h=np.array([d["h"] for d in I], dtype=np.int32),
@@ -414,6 +426,42 @@ def _render_truth(b: _Builder, n, truth, s, pos, rect):
         q = P[0, 0] * dx * dx + 2 * P[0, 1] * dx * dy + P[1, 1] * dy * dy
         acc += wk * np.exp(-0.5 * q) / (2 * math.pi * math.sqrt(np.linalg.det(C)))
     img[y0:y0 + h, x0:x0 + w] += flux * acc
+
+
+def _render_truth_images(b: _Builder, imgs, truth, s, pos, rects):
+    """_render_truth for one source over several same-size rectangles at once."""
+    if not imgs:
+        return
+    d0 = b.img[imgs[0]]
+    h, w = rects[0][3], rects[0][2]
+    A = np.stack([b.img[n]["A"] for n in imgs])                     # [I, 2, 2]
+    t = np.stack([b.img[n]["t"] for n in imgs])
+    psf = np.stack([b.img[n]["psf"] for n in imgs])                 # [I, K, 6]
+    calib = np.array([b.img[n]["calib"] for n in imgs])
+    flux = np.array([_band_flux(truth, s, b.img[n]["band"]) for n in imgs]) * calib
+    mu = A @ pos + t                                                # [I, 2]
+    Cs = A @ _truth_cov(truth, s) @ np.transpose(A, (0, 2, 1))      # [I, 2, 2]
+    x0 = np.array([r[0] for r in rects], dtype=np.float64)
+    y0 = np.array([r[1] for r in rects], dtype=np.float64)
+    xs = x0[:, None, None] + np.arange(w, dtype=np.float64)[None, None, :]
+    ys = y0[:, None, None] + np.arange(h, dtype=np.float64)[None, :, None]
+    acc = np.zeros((len(imgs), h, w))
+    for k in range(N_PSF):
+        wk = psf[:, k, 0]
+        cxx = Cs[:, 0, 0] + psf[:, k, 3]
+        cxy = Cs[:, 0, 1] + psf[:, k, 4]
+        cyy = Cs[:, 1, 1] + psf[:, k, 5]
+        det = cxx * cyy - cxy * cxy
+        dx = xs - (mu[:, 0] + psf[:, k, 1])[:, None, None]
+        dy = ys - (mu[:, 1] + psf[:, k, 2])[:, None, None]
+        q = (cyy[:, None, None] * dx * dx - 2 * cxy[:, None, None] * dx * dy
+             + cxx[:, None, None] * dy * dy) / det[:, None, None]
+        acc += (wk / (2 * math.pi * np.sqrt(det)))[:, None, None] * np.exp(-0.5 * q)
+    for i, n in enumerate(imgs):
+        d = b.img[n]
+        img = b.pix[n].reshape(d["h"], d["stride"])
+        r = rects[i]
+        img[r[1]:r[1] + h, r[0]:r[0] + w] += flux[i] * acc[i]
 
 
 def _rect_for(b, n, pos, side):
@@ -563,12 +611,9 @@ def batched(seed: int = 1803_00113 + 3, n_sources=8192, min_side=15, max_side=10
                                         200.0 * rng.uniform(0.9, 1.1), A, t, _draw_psf(rng)))
         for k in range(g):
             s = s0 + k
-            pl = []
-            for n in imgs:
-                r = _rect_for(b, n, pos[k], sides[k])
-                pl.append((n,) + r)
-                _render_truth(b, n, truth, s, pos[k], r)
-            b.patches.append(pl)
+            rects = [_rect_for(b, n, pos[k], sides[k]) for n in imgs]
+            _render_truth_images(b, imgs, truth, s, pos[k], rects)
+            b.patches.append([(n,) + r for n, r in zip(imgs, rects)])
             pos_all[s] = pos[k]
         _link_neighbours(b, s0, s0 + g)
         s0 += g
