@@ -57,6 +57,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick tile shapes per patch-size bucket before timing (default for batched)")
+    ap.add_argument("--plain-sample", type=int, default=600,
+                    help="sources timed in the plain one-source-per-launch form")
     return ap.parse_args(argv)
 
 
@@ -227,7 +231,12 @@ def run_ours(args):
         ctx = cel.Context(problem.model, device=local, stream=stream)
         dp = cel.DeviceProblem(problem, dev)
         classes = cel.color_classes(problem)
-        plans = [cel.Plan(ctx, dp, c) for c in classes]
+        tiles = None
+        if args.autotune or args.workload == "batched":
+            from paper_1803_00113_gb300.autotune import autotune
+            tiles, tune_report = autotune(ctx, dp, range(problem.n_sources))
+            dp.set_theta(problem.theta)
+        plans = [cel.Plan(ctx, dp, c, ppi_bucket=tiles) for c in classes]
         visits = sum(p.visits for p in plans)
         theta0 = dp.theta.clone()
         delta, status = cel.newton_state(dp)
@@ -330,21 +339,44 @@ def run_ours(args):
         # ---- the plain one-source-per-launch form (same kernels)
         plain = None
         if not args.no_plain and rank == 0:
-            single = [cel.Plan(ctx, dp, [s]) for s in range(problem.n_sources)]
+            order = [int(s) for c in classes for s in c]
+            if len(order) > args.plain_sample:
+                pick = np.linspace(0, len(order) - 1, args.plain_sample).round().astype(int)
+                order = [order[k] for k in pick]
+            single = {s: cel.Plan(ctx, dp, [s]) for s in order}
             reset()
-            for s in range(min(20, problem.n_sources)):
+            for s in order[:20]:
                 cel.newton_step(single[s], delta, status)
             torch.cuda.synchronize(dev)
             reset()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            for c in classes:
-                for s in c:
-                    cel.newton_step(single[int(s)], delta, status)
-                    stream.synchronize()
+            for s in order:
+                cel.newton_step(single[s], delta, status)
+                stream.synchronize()
             plain_s = time.perf_counter() - t0
-            plain = {"value": visits / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
+            pv = problem.visits(order)
+            plain = {"value": pv / plain_s, "unit": UNIT, "sources_timed": len(order),
+                     "ms_per_source": plain_s * 1e3 / len(order),
                      "form": "one source per launch sequence, host sync after each source"}
+            for pl in single.values():
+                pl.close()
+
+        # ---- gradient-only pass vs gradient + Hessian (the paper's cost ratio)
+        big = max(plans, key=lambda p: p.visits)
+        ratio = {}
+        for name, fn in (("grad_hess", cel.elbo_grad_hess), ("grad_only", cel.elbo_grad)):
+            fn(big)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                fn(big)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ratio[name + "_ms"] = a.elapsed_time(b) / 5
+        ratio["hess_over_grad"] = ratio["grad_hess_ms"] / ratio["grad_only_ms"]
+        ratio["visits"] = big.visits
 
     # ---- roofline of the derivative pixel kernel
     props = torch.cuda.get_device_properties(dev)
@@ -364,7 +396,9 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic (seeded fields shaped like the paper's study set)",
         "config": dict(cfg, l2="flushed between steps (256 MB write outside the timed events)",
                        graph=graph is not None, visits_per_step=visits,
-                       colour_classes=len(classes)),
+                       colour_classes=len(classes),
+                       tiles_per_area_bucket=tiles or [256, 256, 256, 256]),
+        "grad_vs_hess": ratio,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

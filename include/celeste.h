@@ -143,13 +143,16 @@ typedef struct celeste_problem {
   int32_t n_images, n_sources, n_patches, n_nbr;
 } celeste_problem;
 
-/* Tile shape of the pixel kernels (picked per patch-size bucket by the
- * autotuner in the Python layer; zeros select the defaults). */
+/* Tile shape of the pixel kernels: the number of pixels one warp reduces
+ * into one item, by patch area bucket ([0, 1024), [1024, 4096),
+ * [4096, 16384), [16384, inf) pixels), picked by the autotuner of the Python
+ * layer.  Zeros select pixels_per_item (itself 0 = 256). */
 typedef struct celeste_tuning {
-  int32_t pixels_per_item;    /* pixels one warp reduces at a time (32..4096) */
-  int32_t warps_per_block;    /* 1..16 */
-  int32_t blocks_per_sm;      /* persistent grid = SMs * blocks_per_sm (0 = max resident) */
+  int32_t pixels_per_item;    /* default pixels per item, 32..65536 */
+  int32_t warps_per_block;    /* reserved (the pixel kernels use 4) */
+  int32_t blocks_per_sm;      /* persistent grid = SMs * blocks_per_sm (0 = 3) */
   int32_t reserved;
+  int32_t ppi_bucket[4];      /* per patch-area bucket, 0 = pixels_per_item */
 } celeste_tuning;
 
 typedef struct celeste_ctx celeste_ctx;

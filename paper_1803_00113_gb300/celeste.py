@@ -52,7 +52,10 @@ class _Problem(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("pixels_per_item", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ppi_bucket", ctypes.c_int32 * 4)]
+
+AREA_BUCKETS = (1024, 4096, 16384)   # patch-area bucket edges of celeste_tuning
 
 
 _LIB = None
@@ -277,12 +280,14 @@ class Plan:
     """Work decomposition and scratch for a list of sources of a problem."""
 
     def __init__(self, ctx: Context, dprob: DeviceProblem, sources: Sequence[int],
-                 pixels_per_item: int = 0, blocks_per_sm: int = 0):
+                 pixels_per_item: int = 0, blocks_per_sm: int = 0, ppi_bucket=None):
         self.ctx = ctx
         self.dprob = dprob
         self.sources = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
         self.n = int(self.sources.size)
         t = _Tuning(pixels_per_item, 0, blocks_per_sm, 0)
+        for k, v in enumerate(ppi_bucket or ()):
+            t.ppi_bucket[k] = int(v)
         h = ctypes.c_void_p()
         _check(lib().celeste_plan_create(ctx.handle, ctypes.byref(dprob.struct),
                                          self.sources.ctypes.data if self.n else None, self.n,

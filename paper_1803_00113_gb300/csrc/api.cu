@@ -324,7 +324,10 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
       bg += area;
       visits += area;
       pi.item_begin = (int)items.size();
-      for (int st = 0; st < area; st += ppi) items.push_back(Item{(int)pairs.size(), st, std::min(ppi, area - st), 0});
+      const int bucket = area < 1024 ? 0 : (area < 4096 ? 1 : (area < 16384 ? 2 : 3));
+      const int bp = tuning && tuning->ppi_bucket[bucket] > 0 ? tuning->ppi_bucket[bucket] : ppi;
+      if (bp < 32 || bp > 65536) return CELESTE_EINVAL;
+      for (int st = 0; st < area; st += bp) items.push_back(Item{(int)pairs.size(), st, std::min(bp, area - st), 0});
       pi.item_end = (int)items.size();
       pairs.push_back(pi);
     }

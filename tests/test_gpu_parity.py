@@ -263,3 +263,19 @@ def test_largest_patch_101(cel):
     p = fields.plain_source(side=101, seed=19)
     (e, er, g, H), _ = _eval(cel, p, [0])
     _check_source(p, 0, e[0], er[0], g[0], H[0], "101x101")
+
+
+def test_autotuned_tiles_give_the_same_results(cel):
+    p = fields.batched(seed=12, n_sources=20, min_side=15, max_side=101, max_images_per_band=2)
+    ctx = _ctx(cel, p)
+    dp = cel.DeviceProblem(p)
+    from paper_1803_00113_gb300.autotune import autotune
+    tiles, report = autotune(ctx, dp, range(p.n_sources), candidates=(64, 256, 1024), reps=1)
+    assert all(t in (0, 64, 256, 1024) for t in tiles) and report
+    ref = cel.elbo_grad_hess(cel.Plan(ctx, dp, list(range(p.n_sources))))
+    got = cel.elbo_grad_hess(cel.Plan(ctx, dp, list(range(p.n_sources)), ppi_bucket=tiles))
+    ctx.synchronize()
+    for a, b in zip(got, ref):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        # only the FP32 summation order differs between tilings
+        assert np.all(np.abs(a - b) <= 1e-5 * np.abs(b) + 1e-6 * np.abs(b).max())

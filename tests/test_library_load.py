@@ -29,6 +29,7 @@ def test_struct_layouts_match_header():
     from paper_1803_00113_gb300 import celeste
     assert celeste.IMAGE_DTYPE.itemsize == 256
     assert celeste.PATCH_DTYPE.itemsize == 32
+    assert ctypes.sizeof(celeste._Tuning) == 32
     assert ctypes.sizeof(celeste._Model) == 4 * 4 + 8 * (32 + 1 + 4 + 16 + 64 + 256 + 6)
 
 
