@@ -283,7 +283,14 @@ def run_ours(args):
         clocks = ClockSampler(local)
         clocks.start()
         l0 = ctx.launches()
-        step_ms, kern_ms, kern_launch, kern_visits = [], 0.0, 0, 0
+        by_kind = {k: [0.0, 0, 0] for k in cel.KERNEL_KINDS}
+
+        def add_kinds(d):
+            for k, (ms, nl, nv) in d.items():
+                by_kind[k][0] += ms
+                by_kind[k][1] += nl
+                by_kind[k][2] += nv
+
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         for k in range(args.steps):
@@ -294,13 +301,11 @@ def run_ours(args):
             ev[k][1].record(stream)
             if graph is not None:
                 stream.synchronize()
-                ms, nl, nv = ctx.profile_read(reset=False)
-                kern_ms += ms
-                kern_launch += nl
-                kern_visits += nv
+                add_kinds(ctx.profile_kernels(reset=False))
         torch.cuda.synchronize(dev)
         if graph is None:
-            kern_ms, kern_launch, kern_visits = ctx.profile_read(reset=True)
+            add_kinds(ctx.profile_kernels(reset=True))
+        kern_ms, kern_launch, kern_visits = by_kind["derivs"]
         n_launch = ctx.launches() - l0
         if graph is not None:
             # a replay launches the captured kernels: count them per step
@@ -312,6 +317,17 @@ def run_ours(args):
         total_s = reduce_max(sum(step_ms) / 1e3, world, dev)
         all_visits = reduce_sum(visits * args.steps, world, dev)
         value = all_visits / total_s
+
+        # ---- per-kernel breakdown of one step (eager, every kind timed; kept
+        # out of the timed region, where only the derivative kernel is timed)
+        ctx.profile(True, kinds="all")
+        reset()
+        flush.zero_()
+        step()
+        torch.cuda.synchronize(dev)
+        breakdown = {k: {"ms": ms, "launches": nl} for k, (ms, nl, _) in
+                     ctx.profile_kernels(reset=True).items() if nl}
+        ctx.profile(False)
 
         # ---- end to end through the public API, host buffers
         pin_pix = torch.from_numpy(problem.pixels).pin_memory()
@@ -338,6 +354,7 @@ def run_ours(args):
 
         # ---- the plain one-source-per-launch form (same kernels)
         plain = None
+        ctx.profile(False)
         if not args.no_plain and rank == 0:
             order = [int(s) for c in classes for s in c]
             if len(order) > args.plain_sample:
@@ -362,21 +379,30 @@ def run_ours(args):
             for pl in single.values():
                 pl.close()
 
-        # ---- gradient-only pass vs gradient + Hessian (the paper's cost ratio)
+        # ---- gradient-only pass vs gradient + Hessian (the paper's cost ratio):
+        # whole calls, and the pixel kernels alone (the calls share the
+        # neighbour-background kernel, which is the same work in both)
         big = max(plans, key=lambda p: p.visits)
-        ratio = {}
-        for name, fn in (("grad_hess", cel.elbo_grad_hess), ("grad_only", cel.elbo_grad)):
+        ratio = {"visits": big.visits}
+        for name, fn, kind in (("grad_hess", cel.elbo_grad_hess, "derivs"),
+                               ("grad_only", cel.elbo_grad, "grad")):
             fn(big)
             torch.cuda.synchronize(dev)
+            ctx.profile(True, kinds="all")
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(5):
                 fn(big)
             b.record(stream)
             torch.cuda.synchronize(dev)
-            ratio[name + "_ms"] = a.elapsed_time(b) / 5
-        ratio["hess_over_grad"] = ratio["grad_hess_ms"] / ratio["grad_only_ms"]
-        ratio["visits"] = big.visits
+            kinds = ctx.profile_kernels(reset=True)
+            ctx.profile(False)
+            ratio[name + "_call_ms"] = a.elapsed_time(b) / 5
+            ratio[name + "_pixel_kernel_ms"] = kinds[kind][0] / max(kinds[kind][1], 1)
+            ratio[name + "_epilogue_ms"] = kinds["epilogue"][0] / max(kinds["epilogue"][1], 1)
+        ratio["hess_over_grad_call"] = ratio["grad_hess_call_ms"] / ratio["grad_only_call_ms"]
+        ratio["hess_over_grad_pixel_kernel"] = (ratio["grad_hess_pixel_kernel_ms"]
+                                                / ratio["grad_only_pixel_kernel_ms"])
 
     # ---- roofline of the derivative pixel kernel
     props = torch.cuda.get_device_properties(dev)
@@ -399,6 +425,7 @@ def run_ours(args):
                        colour_classes=len(classes),
                        tiles_per_area_bucket=tiles or [256, 256, 256, 256]),
         "grad_vs_hess": ratio,
+        "kernels_one_step": breakdown,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

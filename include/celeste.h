@@ -168,18 +168,33 @@ int celeste_destroy(celeste_ctx* ctx);
 int celeste_synchronize(celeste_ctx* ctx, uint32_t* device_error);
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t celeste_launch_count(const celeste_ctx* ctx);
-/* Event timing of the derivative pixel kernel (the dominant kernel of
- * celeste_elbo_grad_hess and celeste_newton_step): when enabled, every
- * launch is bracketed by a pair of CUDA events recorded on the context's
- * stream (enabling also clears the list of pairs; events are reused).
- * celeste_profile_read synchronises the stream and returns the summed
- * kernel time (ms) over the recorded pairs, their number and the
- * source-pixel visits they processed; reset != 0 clears the list.  A CUDA
- * graph captured with timing enabled records the same pairs on every
- * replay: read with reset = 0 after each replay. */
+/* Event timing of kernel launches: when enabled, every launch of a timed
+ * kind is bracketed by a pair of CUDA events recorded on the context's
+ * stream (enabling also clears the list of pairs; events are reused).  on
+ * is a mask of (1 << CELESTE_K_*) bits: 0 disables, -1 times every kind.
+ * celeste_profile_read synchronises the stream and returns, for the
+ * derivative pixel kernel (the dominant kernel of celeste_elbo_grad_hess
+ * and celeste_newton_step), the summed kernel time (ms) over the recorded
+ * pairs, their number and the source-pixel visits they processed; reset !=
+ * 0 clears the list.  A CUDA graph captured with timing enabled records the
+ * same pairs on every replay: read with reset = 0 after each replay.
+ * Launches inside a region fit (celeste_fit_run) are never timed. */
 int celeste_profile_enable(celeste_ctx* ctx, int on);
 int celeste_profile_read(celeste_ctx* ctx, int reset, double* total_ms, int64_t* launches,
                          int64_t* visits);
+/* The same timing for every kernel kind: ms[k], launches[k] and (for pixel
+ * kernels) visits[k] for k < CELESTE_K_COUNT; visits may be NULL. */
+#define CELESTE_K_SETUP       0
+#define CELESTE_K_BACKGROUND  1
+#define CELESTE_K_DERIVS      2   /* value + gradient + Hessian pixel pass */
+#define CELESTE_K_GRAD        3   /* value + gradient pixel pass */
+#define CELESTE_K_VALUE       4   /* value-only pixel pass */
+#define CELESTE_K_EPILOGUE    5
+#define CELESTE_K_TRSTEP      6
+#define CELESTE_K_OTHER       7
+#define CELESTE_K_COUNT       8
+int celeste_profile_kernels(celeste_ctx* ctx, int reset, double* ms, int64_t* launches,
+                            int64_t* visits);
 
 /* A plan binds a list of sources of a problem to a work decomposition
  * (per source, image and pixel tile) and owns the device scratch of the
@@ -215,7 +230,7 @@ int celeste_elbo_grad(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, 
 int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, double* elbo_rel);
 
 /* One trust-region Newton iteration (Sec. 4.3) on every source of the plan
- * whose status is not CONVERGED/FAILED: evaluate L_s, g, H at theta; solve
+ * whose status is not CONVERGED/FAILED/MAXITER: evaluate L_s, g, H at theta; solve
  * max g.p + p.H.p/2 s.t. |p| <= delta exactly in FP64; evaluate L_s at
  * theta + p; accept when the ratio of actual to predicted gain exceeds 0.1;
  * update the radius (shrink to |p|/4 below 1/4, double up to 100 above 3/4
@@ -231,6 +246,40 @@ int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, doubl
 #define CELESTE_ST_FAILED    (-1)
 int celeste_newton_step(celeste_ctx* ctx, const celeste_plan* plan,
                         double* delta, int32_t* status, double* elbo_rel);
+
+/* Block coordinate ascent over a region (Sec. 4.3, 4.4): a fit object
+ * colours the overlap graph of the n sources h_src_ids (HOST array,
+ * distinct ids) greedily in ascending id (two region sources conflict when
+ * one is in the other's neighbour list) and holds one plan per colour class
+ * plus the per-source Newton state.  Sources outside the region stay fixed
+ * and only enter as neighbours.  tuning may be NULL. */
+typedef struct celeste_fit celeste_fit;
+int celeste_fit_create(celeste_ctx* ctx, const celeste_problem* problem,
+                       const int32_t* h_src_ids, int32_t n, const celeste_tuning* tuning,
+                       celeste_fit** out);
+int celeste_fit_destroy(celeste_fit* fit);
+/* Number of colour classes of the region. */
+int celeste_fit_classes(const celeste_fit* fit);
+/* Runs the fit: passes over the classes in ascending colour; in a pass each
+ * source gets one fresh subsolver call (radius 1, status 0) of at most
+ * max_iter trust-region Newton iterations (celeste_newton_step's
+ * iteration) with every other source at its current value; the neighbour
+ * background of a class is rendered once per pass.  Within a class the
+ * iterations run on the device (a CUDA graph loop per class, no host
+ * round trip); the host waits once per pass.  The fit stops after the first
+ * pass whose total ELBO gain (the sum of the actual gains of its accepted
+ * steps) is at most pass_tol times the region's source count, or after
+ * max_passes passes.  0 selects max_passes = 5, max_iter = 50 (both at most
+ * 1000).  Updates problem->theta of the region's sources in place.  Host
+ * outputs (may be NULL): *passes_out, pass_gain[max_passes]. */
+int celeste_fit_run(celeste_ctx* ctx, celeste_fit* fit, int32_t max_passes, int32_t max_iter,
+                    double pass_tol, int32_t* passes_out, double* pass_gain);
+/* Per-source results of the last run, DEVICE arrays indexed by source id
+ * ([n_sources], entries of sources outside the region are unspecified; each
+ * may be NULL): status of the last subsolver call (CELESTE_ST_*), Newton
+ * iterations and accepted steps over all passes, final trust radius. */
+int celeste_fit_results(celeste_ctx* ctx, const celeste_fit* fit, int32_t* status,
+                        int32_t* iters, int32_t* accepted, double* delta);
 
 /* Only the FP64 trust-region subproblem, for n independent problems:
  * maximise g.p + p.H.p/2 subject to |p| <= delta (Sec. 4.3).  g[n][27],

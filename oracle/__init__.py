@@ -10,4 +10,5 @@ from .elbo import (  # noqa: F401
     Theta, PatchData, gather_patches, source_elbo, source_elbo_parts, elbo_grad_hess,
     abs_sum_scales, render_source_patch, background_patch, kl_source, band_moments,
     galaxy_covariance, pixel_term, full_field_elbo)
-from .newton import tr_subproblem, newton_iteration, newton_fit  # noqa: F401
+from .newton import (  # noqa: F401
+    tr_subproblem, newton_iteration, newton_fit, overlap_classes, region_fit)

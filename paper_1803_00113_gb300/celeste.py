@@ -78,6 +78,7 @@ def lib():
         "celeste_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "celeste_profile_read": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(D),
                                                 ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "celeste_profile_kernels": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
         "celeste_plan_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem), P, I32,
                                                ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
         "celeste_plan_destroy": (ctypes.c_int, [P]),
@@ -90,6 +91,12 @@ def lib():
         "celeste_render": (ctypes.c_int, [P, P, P, P]),
         "celeste_background": (ctypes.c_int, [P, P, P, P]),
         "celeste_color_sources": (ctypes.c_int, [I32, P, P, P]),
+        "celeste_fit_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem), P, I32,
+                                              ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
+        "celeste_fit_destroy": (ctypes.c_int, [P]),
+        "celeste_fit_classes": (ctypes.c_int, [P]),
+        "celeste_fit_run": (ctypes.c_int, [P, P, I32, I32, D, ctypes.POINTER(I32), P]),
+        "celeste_fit_results": (ctypes.c_int, [P, P, P, P, P, P]),
         "celeste_elbo_grad_hess_noalloc": (ctypes.c_int, [ctypes.POINTER(_Model),
                                                           ctypes.POINTER(_Problem), P, I32, P,
                                                           P, P, P, P, P]),
@@ -105,11 +112,16 @@ def lib():
 def exported_symbols():
     """Names the header declares, for the load check."""
     return ["celeste_create", "celeste_destroy", "celeste_synchronize", "celeste_launch_count",
-            "celeste_profile_enable", "celeste_profile_read",
+            "celeste_profile_enable", "celeste_profile_read", "celeste_profile_kernels",
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
             "celeste_elbo_grad_hess", "celeste_elbo", "celeste_elbo_grad", "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
-            "celeste_color_sources", "celeste_elbo_grad_hess_noalloc"]
+            "celeste_color_sources", "celeste_fit_create", "celeste_fit_destroy",
+            "celeste_fit_classes", "celeste_fit_run", "celeste_fit_results",
+            "celeste_elbo_grad_hess_noalloc"]
+
+
+KERNEL_KINDS = ("setup", "background", "derivs", "grad", "value", "epilogue", "tr_step", "other")
 
 
 class CelesteError(RuntimeError):
@@ -178,8 +190,16 @@ class Context:
     def launches(self) -> int:
         return int(lib().celeste_launch_count(self.handle))
 
-    def profile(self, on: bool):
-        _check(lib().celeste_profile_enable(self.handle, 1 if on else 0), "celeste_profile_enable")
+    def profile(self, on, kinds=None):
+        """Event timing: off, the derivative kernel only (on=True), or the
+        named kernel kinds (kinds="all" or an iterable of KERNEL_KINDS)."""
+        if not on:
+            mode = 0
+        elif kinds == "all":
+            mode = -1
+        else:
+            mode = sum(1 << KERNEL_KINDS.index(k) for k in (kinds or ("derivs",)))
+        _check(lib().celeste_profile_enable(self.handle, mode), "celeste_profile_enable")
 
     def profile_read(self, reset: bool = True):
         """(kernel ms, timed launches, visits) of the derivative kernel."""
@@ -190,6 +210,17 @@ class Context:
                                           ctypes.byref(n), ctypes.byref(vis)),
                "celeste_profile_read")
         return ms.value, n.value, vis.value
+
+    def profile_kernels(self, reset: bool = True):
+        """{kind: (ms, launches, visits)} of every timed kernel kind."""
+        k = len(KERNEL_KINDS)
+        ms = np.zeros(k)
+        n = np.zeros(k, dtype=np.int64)
+        vis = np.zeros(k, dtype=np.int64)
+        _check(lib().celeste_profile_kernels(self.handle, 1 if reset else 0, ms.ctypes.data,
+                                             n.ctypes.data, vis.ctypes.data),
+               "celeste_profile_kernels")
+        return {name: (float(ms[i]), int(n[i]), int(vis[i])) for i, name in enumerate(KERNEL_KINDS)}
 
     def close(self):
         if getattr(self, "handle", None):
@@ -401,6 +432,58 @@ def color_sources(nbr_ptr: np.ndarray, nbr_idx: np.ndarray) -> np.ndarray:
 def color_classes(problem) -> list:
     col = color_sources(problem.nbr_ptr, problem.nbr_idx)
     return [np.flatnonzero(col == c).astype(np.int32) for c in range(int(col.max()) + 1 if len(col) else 0)]
+
+
+class Fit:
+    """Block coordinate ascent over a region of sources (celeste_fit_*)."""
+
+    def __init__(self, ctx: Context, dprob: DeviceProblem, sources: Sequence[int],
+                 pixels_per_item: int = 0, ppi_bucket=None):
+        self.ctx = ctx
+        self.dprob = dprob
+        self.sources = np.ascontiguousarray(np.asarray(sorted(sources), dtype=np.int32))
+        t = _Tuning(pixels_per_item, 0, 0, 0)
+        for k, v in enumerate(ppi_bucket or ()):
+            t.ppi_bucket[k] = int(v)
+        h = ctypes.c_void_p()
+        _check(lib().celeste_fit_create(ctx.handle, ctypes.byref(dprob.struct),
+                                        self.sources.ctypes.data if self.sources.size else None,
+                                        int(self.sources.size), ctypes.byref(t), ctypes.byref(h)),
+               "celeste_fit_create")
+        self.handle = h
+        self.n_classes = int(lib().celeste_fit_classes(h))
+
+    def run(self, max_passes: int = 5, max_iter: int = 50, pass_tol: float = 1e-3):
+        """Runs the fit; returns (passes, [gain of each pass])."""
+        passes = ctypes.c_int32(0)
+        gains = np.zeros(max(max_passes, 1), dtype=np.float64)
+        _check(lib().celeste_fit_run(self.ctx.handle, self.handle, int(max_passes), int(max_iter),
+                                     float(pass_tol), ctypes.byref(passes), gains.ctypes.data),
+               "celeste_fit_run")
+        return int(passes.value), gains[:passes.value].tolist()
+
+    def results(self):
+        """(status, iterations, accepted steps, radius): [n_sources] device tensors."""
+        dev = self.ctx.device
+        S = self.dprob.n_sources
+        st = torch.zeros(S, dtype=torch.int32, device=dev)
+        it = torch.zeros(S, dtype=torch.int32, device=dev)
+        acc = torch.zeros(S, dtype=torch.int32, device=dev)
+        dl = torch.zeros(S, dtype=torch.float64, device=dev)
+        _check(lib().celeste_fit_results(self.ctx.handle, self.handle, _ptr(st), _ptr(it),
+                                         _ptr(acc), _ptr(dl)), "celeste_fit_results")
+        return st, it, acc, dl
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_fit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def elbo_grad_hess_noalloc(model, dprob: DeviceProblem, sources: Sequence[int], out,

@@ -21,11 +21,12 @@ struct celeste_ctx {
   unsigned int* d_err = nullptr;
   int n_exp = 0, n_dev = 0;
   int64_t launches = 0;
-  // event timing of the derivative pixel kernel (celeste_profile_*)
-  bool profiling = false;
+  // event timing of kernel launches by kind (celeste_profile_*)
+  unsigned profiling = 0;            // bit k: time kernels of kind k
   std::vector<cudaEvent_t> events;   // start/stop pairs, reused
-  size_t n_timed = 0;                // pairs recorded since the last read
-  int64_t timed_visits = 0;
+  std::vector<int> kinds;            // kind of pair k
+  std::vector<int64_t> visits;       // visits of pair k (pixel kernels)
+  size_t n_timed = 0;                // pairs recorded since the last reset
 };
 
 struct celeste_plan {
@@ -36,6 +37,20 @@ struct celeste_plan {
   std::vector<void*> allocs;
   int64_t visits = 0;
   celeste_tuning tuning{};
+};
+
+struct celeste_fit {
+  celeste_ctx* ctx = nullptr;
+  std::vector<int32_t> region;              // sorted source ids
+  std::vector<celeste_plan*> plans;         // one per colour class
+  std::vector<void*> allocs;
+  FitView f{};
+  double* h_out = nullptr;                  // pinned copy of f.out
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int built_max_iter = 0;
+  int n_sources = 0;
 };
 
 namespace {
@@ -110,9 +125,12 @@ T* dev_alloc(celeste_plan* p, size_t count, int* err) {
   return static_cast<T*>(ptr);
 }
 
-// Launches the derivative pixel kernel, bracketed by events when profiling.
-cudaError_t derivs_launch(celeste_ctx* c, celeste_plan* p, const Launch& L) {
-  if (!c->profiling) return launch_pixels_derivs(L, p->v);
+// Runs one launch, bracketed by a pair of events when profiling (under
+// stream capture an ordinary record only expresses a dependency; the
+// external flag makes it an event-record node of the graph).
+template <typename F>
+cudaError_t timed(celeste_ctx* c, int kind, int64_t visits, cudaStream_t stream, F&& launch) {
+  if (!(c->profiling >> kind & 1u)) return launch();
   if (2 * (c->n_timed + 1) > c->events.size()) {
     for (int k = 0; k < 2; ++k) {
       cudaEvent_t e;
@@ -120,27 +138,33 @@ cudaError_t derivs_launch(celeste_ctx* c, celeste_plan* p, const Launch& L) {
       if (r != cudaSuccess) return r;
       c->events.push_back(e);
     }
+    c->kinds.push_back(0);
+    c->visits.push_back(0);
   }
   cudaEvent_t e0 = c->events[2 * c->n_timed], e1 = c->events[2 * c->n_timed + 1];
-  // under stream capture an ordinary record only expresses a dependency;
-  // the external flag makes it an event-record node of the graph
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaError_t r = cudaStreamIsCapturing(L.stream, &cap);
+  cudaError_t r = cudaStreamIsCapturing(stream, &cap);
   const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
-  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e0, L.stream, flags);
-  if (r == cudaSuccess) r = launch_pixels_derivs(L, p->v);
-  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e1, L.stream, flags);
+  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e0, stream, flags);
+  if (r == cudaSuccess) r = launch();
+  if (r == cudaSuccess) r = cudaEventRecordWithFlags(e1, stream, flags);
   if (r == cudaSuccess) {
+    c->kinds[c->n_timed] = kind;
+    c->visits[c->n_timed] = visits;
     ++c->n_timed;
-    c->timed_visits += p->visits;
   }
   return r;
+}
+
+cudaError_t derivs_launch(celeste_ctx* c, celeste_plan* p, const Launch& L) {
+  return timed(c, CELESTE_K_DERIVS, p->visits, L.stream, [&] { return launch_pixels_derivs(L, p->v); });
 }
 
 int run_setup(celeste_ctx* c, celeste_plan* p, int first, int n, bool trial) {
   Launch L = make_launch(c, p);
   ++c->launches;
-  return to_status(launch_setup(L, p->v, c->d_model, first, n, trial));
+  return to_status(timed(c, CELESTE_K_SETUP, 0, L.stream,
+                         [&] { return launch_setup(L, p->v, c->d_model, first, n, trial); }));
 }
 
 }  // namespace
@@ -250,29 +274,42 @@ int64_t celeste_launch_count(const celeste_ctx* c) { return c ? c->launches : -1
 
 int celeste_profile_enable(celeste_ctx* c, int on) {
   if (!c) return CELESTE_EINVAL;
-  c->profiling = on != 0;
+  c->profiling = static_cast<unsigned>(on) & ((1u << CELESTE_K_COUNT) - 1u);
   c->n_timed = 0;
-  c->timed_visits = 0;
+  return CELESTE_OK;
+}
+
+int celeste_profile_kernels(celeste_ctx* c, int reset, double* ms, int64_t* launches,
+                            int64_t* visits) {
+  if (!c || !ms || !launches) return CELESTE_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < CELESTE_K_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    if (visits) visits[k] = 0;
+  }
+  for (size_t k = 0; k < c->n_timed; ++k) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->events[2 * k], c->events[2 * k + 1]));
+    const int kind = c->kinds[k];
+    ms[kind] += t;
+    ++launches[kind];
+    if (visits) visits[kind] += c->visits[k];
+  }
+  if (reset) c->n_timed = 0;
   return CELESTE_OK;
 }
 
 int celeste_profile_read(celeste_ctx* c, int reset, double* total_ms, int64_t* launches,
                          int64_t* visits) {
   if (!c || !total_ms || !launches || !visits) return CELESTE_EINVAL;
-  CK(cudaStreamSynchronize(c->stream));
-  double ms = 0.0;
-  for (size_t k = 0; k < c->n_timed; ++k) {
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, c->events[2 * k], c->events[2 * k + 1]));
-    ms += t;
-  }
-  *total_ms = ms;
-  *launches = (int64_t)c->n_timed;
-  *visits = c->timed_visits;
-  if (reset) {
-    c->n_timed = 0;
-    c->timed_visits = 0;
-  }
+  double ms[CELESTE_K_COUNT];
+  int64_t n[CELESTE_K_COUNT], vis[CELESTE_K_COUNT];
+  const int rc = celeste_profile_kernels(c, reset, ms, n, vis);
+  if (rc) return rc;
+  *total_ms = ms[CELESTE_K_DERIVS];
+  *launches = n[CELESTE_K_DERIVS];
+  *visits = vis[CELESTE_K_DERIVS];
   return CELESTE_OK;
 }
 
@@ -460,8 +497,9 @@ static int eval_common(celeste_ctx* c, celeste_plan* p, bool derivs) {
   int rc = run_setup(c, p, 0, p->v.n_pairs, false);
   if (rc) return rc;
   c->launches += 2;
-  CK(launch_background(L, p->v));
-  CK(derivs ? derivs_launch(c, p, L) : launch_pixels_value(L, p->v));
+  CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, p->v); }));
+  CK(derivs ? derivs_launch(c, p, L)
+            : timed(c, CELESTE_K_VALUE, p->visits, L.stream, [&] { return launch_pixels_value(L, p->v); }));
   return CELESTE_OK;
 }
 
@@ -475,7 +513,9 @@ int celeste_elbo_grad_hess(celeste_ctx* c, const celeste_plan* pc, double* elbo,
   if (rc) return rc;
   Launch L = make_launch(c, p);
   ++c->launches;
-  return to_status(launch_epilogue(L, p->v, c->d_model, elbo, elbo_rel, grad, hess));
+  return to_status(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
+    return launch_epilogue(L, p->v, c->d_model, elbo, elbo_rel, grad, hess);
+  }));
 }
 
 int celeste_elbo_grad(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel,
@@ -489,9 +529,11 @@ int celeste_elbo_grad(celeste_ctx* c, const celeste_plan* pc, double* elbo, doub
   int rc = run_setup(c, p, 0, p->v.n_pairs, false);
   if (rc) return rc;
   c->launches += 3;
-  CK(launch_background(L, p->v));
-  CK(launch_pixels_grad(L, p->v));
-  return to_status(launch_epilogue_grad(L, p->v, c->d_model, elbo, elbo_rel, grad));
+  CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, p->v); }));
+  CK(timed(c, CELESTE_K_GRAD, p->visits, L.stream, [&] { return launch_pixels_grad(L, p->v); }));
+  return to_status(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
+    return launch_epilogue_grad(L, p->v, c->d_model, elbo, elbo_rel, grad);
+  }));
 }
 
 int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* elbo_rel) {
@@ -502,8 +544,29 @@ int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* e
   if (rc) return rc;
   Launch L = make_launch(c, p);
   ++c->launches;
-  return to_status(launch_epilogue_value(L, p->v, c->d_model, elbo, elbo_rel, false));
+  return to_status(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
+    return launch_epilogue_value(L, p->v, c->d_model, elbo, elbo_rel, false);
+  }));
 }
+
+// One trust-region Newton iteration of the plan's active sources once the
+// neighbour records and background are in place: own records, derivative
+// pass, epilogue, FP64 step, trial records, trial value, accept.
+static cudaError_t enqueue_iteration(celeste_ctx* c, celeste_plan* p, const Launch& L,
+                                     double* delta, int32_t* status) {
+  PlanView& v = p->v;
+  cudaError_t e = launch_mark_active(L, v, status);
+  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, false);
+  if (e == cudaSuccess) e = launch_pixels_derivs(L, v);
+  if (e == cudaSuccess) e = launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
+  if (e == cudaSuccess) e = launch_tr_step(L, v, delta, status);
+  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, true);
+  if (e == cudaSuccess) e = launch_pixels_value(L, v);
+  if (e == cudaSuccess) e = launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
+  if (e == cudaSuccess) e = launch_tr_accept(L, v, p->rel_trial, delta, status);
+  return e;
+}
+constexpr int kIterationLaunches = 10;   // enqueue_iteration + fit_check
 
 int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, int32_t* status,
                         double* elbo_rel) {
@@ -513,22 +576,27 @@ int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, i
   Launch L = make_launch(c, p);
   PlanView& v = p->v;
   c->launches += 1;
-  CK(launch_mark_active(L, v, status));
+  CK(timed(c, CELESTE_K_OTHER, 0, L.stream, [&] { return launch_mark_active(L, v, status); }));
   int rc = run_setup(c, p, 0, v.n_pairs, false);
   if (rc) return rc;
   c->launches += 3;
-  CK(launch_background(L, v));
+  CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, v); }));
   CK(derivs_launch(c, p, L));
-  CK(launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess));
+  CK(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
+    return launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
+  }));
   if (elbo_rel) CK(cudaMemcpyAsync(elbo_rel, v.elbo_rel, v.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   c->launches += 1;
-  CK(launch_tr_step(L, v, delta, status));
+  CK(timed(c, CELESTE_K_TRSTEP, 0, L.stream, [&] { return launch_tr_step(L, v, delta, status); }));
   rc = run_setup(c, p, 0, v.n_own_pairs, true);
   if (rc) return rc;
   c->launches += 3;
-  CK(launch_pixels_value(L, v));
-  CK(launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true));
-  CK(launch_tr_accept(L, v, p->rel_trial, delta, status));
+  CK(timed(c, CELESTE_K_VALUE, p->visits, L.stream, [&] { return launch_pixels_value(L, v); }));
+  CK(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
+    return launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
+  }));
+  CK(timed(c, CELESTE_K_OTHER, 0, L.stream,
+           [&] { return launch_tr_accept(L, v, p->rel_trial, delta, status); }));
   return CELESTE_OK;
 }
 
@@ -581,6 +649,228 @@ int celeste_color_sources(int32_t n, const int32_t* nbr_ptr, const int32_t* nbr_
     n_colors = std::max(n_colors, col + 1);
   }
   return n_colors;
+}
+
+
+// ---- region fit -----------------------------------------------------------
+
+int celeste_fit_destroy(celeste_fit* F) {
+  if (!F) return CELESTE_EINVAL;
+  if (F->exec) cudaGraphExecDestroy(F->exec);
+  if (F->graph) cudaGraphDestroy(F->graph);
+  if (F->capture) cudaStreamDestroy(F->capture);
+  if (F->h_out) cudaFreeHost(F->h_out);
+  for (celeste_plan* p : F->plans) celeste_plan_destroy(p);
+  for (void* a : F->allocs) cudaFree(a);
+  delete F;
+  return CELESTE_OK;
+}
+
+int celeste_fit_create(celeste_ctx* c, const celeste_problem* pr, const int32_t* ids, int32_t n,
+                       const celeste_tuning* tuning, celeste_fit** out) {
+  if (!c || !pr || !out || n < 0 || (n > 0 && !ids) || !pr->h_nbr_ptr ||
+      (pr->n_nbr > 0 && !pr->h_nbr_idx))
+    return CELESTE_EINVAL;
+  *out = nullptr;
+  std::vector<int32_t> region(ids, ids + n);
+  std::sort(region.begin(), region.end());
+  for (int j = 0; j < n; ++j)
+    if (region[j] < 0 || region[j] >= pr->n_sources || (j > 0 && region[j] == region[j - 1]))
+      return CELESTE_EINVAL;
+  // greedy colouring of the region's overlap graph by ascending id
+  std::vector<int32_t> color(pr->n_sources, -1);
+  int n_colors = 0;
+  std::vector<char> used;
+  for (int s : region) {
+    used.assign(n_colors + 1, 0);
+    for (int k = pr->h_nbr_ptr[s]; k < pr->h_nbr_ptr[s + 1]; ++k) {
+      const int t = pr->h_nbr_idx[k];
+      if (t < 0 || t >= pr->n_sources) return CELESTE_EINVAL;
+      if (color[t] >= 0) used[color[t]] = 1;
+    }
+    int col = 0;
+    while (used[col]) ++col;
+    color[s] = col;
+    n_colors = std::max(n_colors, col + 1);
+  }
+  celeste_fit* F = new celeste_fit();
+  F->ctx = c;
+  F->region = region;
+  F->n_sources = pr->n_sources;
+  int rc = CELESTE_OK;
+  for (int col = 0; col < n_colors && rc == CELESTE_OK; ++col) {
+    std::vector<int32_t> cls;
+    for (int s : region)
+      if (color[s] == col) cls.push_back(s);
+    celeste_plan* p = nullptr;
+    rc = celeste_plan_create(c, pr, cls.data(), (int)cls.size(), tuning, &p);
+    if (rc == CELESTE_OK) F->plans.push_back(p);
+  }
+  auto alloc = [&](size_t bytes) -> void* {
+    void* ptr = nullptr;
+    if (rc != CELESTE_OK) return nullptr;
+    if (cudaMalloc(&ptr, bytes ? bytes : 1) != cudaSuccess) {
+      rc = CELESTE_ENOMEM;
+      return nullptr;
+    }
+    F->allocs.push_back(ptr);
+    return ptr;
+  };
+  const size_t S = (size_t)pr->n_sources;
+  FitView& f = F->f;
+  int32_t* d_region = static_cast<int32_t*>(alloc(n * sizeof(int32_t)));
+  f.delta = static_cast<double*>(alloc(S * sizeof(double)));
+  f.status = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
+  f.iters_pass = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
+  f.iters_total = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
+  f.accepted = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
+  f.done = static_cast<uint8_t*>(alloc(S));
+  f.gain = static_cast<double*>(alloc(S * sizeof(double)));
+  f.class_iter = static_cast<int32_t*>(alloc(n_colors * sizeof(int32_t)));
+  f.out = static_cast<double*>(alloc((1 + n_colors) * sizeof(double)));
+  f.region = d_region;
+  f.n_region = n;
+  f.n_classes = n_colors;
+  if (rc == CELESTE_OK &&
+      (cudaMallocHost(&F->h_out, (1 + n_colors) * sizeof(double)) != cudaSuccess ||
+       cudaMemcpy(d_region, region.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemset(f.iters_total, 0, S * sizeof(int32_t)) != cudaSuccess ||
+       cudaMemset(f.accepted, 0, S * sizeof(int32_t)) != cudaSuccess ||
+       cudaMemset(f.status, 0, S * sizeof(int32_t)) != cudaSuccess ||
+       cudaStreamCreateWithFlags(&F->capture, cudaStreamNonBlocking) != cudaSuccess))
+    rc = CELESTE_ECUDA;
+  if (rc != CELESTE_OK) {
+    celeste_fit_destroy(F);
+    return rc;
+  }
+  *out = F;
+  return CELESTE_OK;
+}
+
+int celeste_fit_classes(const celeste_fit* F) { return F ? F->f.n_classes : -1; }
+
+// Builds the graph of one pass (see fit.cu) for the given iteration budget.
+static int fit_build(celeste_fit* F, int max_iter) {
+  celeste_ctx* c = F->ctx;
+  if (F->exec) cudaGraphExecDestroy(F->exec);
+  if (F->graph) cudaGraphDestroy(F->graph);
+  F->exec = nullptr;
+  F->graph = nullptr;
+  F->f.max_iter = max_iter;
+  const FitView f = F->f;
+  cudaStream_t cs = F->capture;
+  CK(cudaGraphCreate(&F->graph, 0));
+  std::vector<cudaGraphNode_t> deps;
+  auto begin = [&]() {
+    return cudaStreamBeginCaptureToGraph(cs, F->graph, deps.empty() ? nullptr : deps.data(),
+                                         nullptr, deps.size(), cudaStreamCaptureModeRelaxed);
+  };
+  auto end = [&]() {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd);
+    if (e == cudaSuccess) deps.assign(d, d + nd);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    return e != cudaSuccess ? e : e2;
+  };
+  CK(begin());
+  cudaError_t e = launch_fit_reset(cs, f);
+  cudaError_t e2 = end();
+  CK(e);
+  CK(e2);
+  for (int k = 0; k < f.n_classes; ++k) {
+    celeste_plan* p = F->plans[k];
+    Launch L = make_launch(c, p);
+    L.stream = cs;
+    // neighbour records and background, once per class and pass
+    CK(begin());
+    e = launch_mark_active(L, p->v, f.status);
+    if (e == cudaSuccess) e = launch_setup(L, p->v, c->d_model, 0, p->v.n_pairs, false);
+    if (e == cudaSuccess) e = launch_background(L, p->v);
+    e2 = end();
+    CK(e);
+    CK(e2);
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, F->graph, 1, cudaGraphCondAssignDefault));
+    // (the parameter union has no default constructor: zeroed storage)
+    alignas(cudaGraphNodeParams) unsigned char np_bytes[sizeof(cudaGraphNodeParams)];
+    memset(np_bytes, 0, sizeof(np_bytes));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_bytes);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t loop;
+    CK(cudaGraphAddNode(&loop, F->graph, deps.empty() ? nullptr : deps.data(), nullptr,
+                        deps.size(), &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    e = enqueue_iteration(c, p, L, f.delta, f.status);
+    if (e == cudaSuccess) e = launch_fit_check(cs, p->v, f, p->rel_trial, k, h);
+    cudaGraph_t g = nullptr;
+    e2 = cudaStreamEndCapture(cs, &g);
+    CK(e);
+    CK(e2);
+    deps.assign(1, loop);
+  }
+  CK(begin());
+  e = launch_fit_pass_end(cs, f);
+  e2 = end();
+  CK(e);
+  CK(e2);
+  CK(cudaGraphInstantiate(&F->exec, F->graph, 0));
+  F->built_max_iter = max_iter;
+  return CELESTE_OK;
+}
+
+int celeste_fit_run(celeste_ctx* c, celeste_fit* F, int32_t max_passes, int32_t max_iter,
+                    double pass_tol, int32_t* passes_out, double* pass_gain) {
+  if (!c || !F || F->ctx != c || max_passes < 0 || max_passes > 1000 || max_iter < 0 ||
+      max_iter > 1000 || !(pass_tol >= 0.0))
+    return CELESTE_EINVAL;
+  if (max_passes == 0) max_passes = 5;
+  if (max_iter == 0) max_iter = 50;
+  if (passes_out) *passes_out = 0;
+  if (F->f.n_region == 0) return CELESTE_OK;
+  if (!F->exec || F->built_max_iter != max_iter) {
+    const int rc = fit_build(F, max_iter);
+    if (rc) return rc;
+  }
+  const FitView& f = F->f;
+  const size_t S = (size_t)F->n_sources;
+  CK(cudaMemsetAsync(f.iters_total, 0, S * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(f.accepted, 0, S * sizeof(int32_t), c->stream));
+  int pass = 0;
+  while (pass < max_passes) {
+    CK(cudaGraphLaunch(F->exec, c->stream));
+    CK(cudaMemcpyAsync(F->h_out, f.out, (1 + f.n_classes) * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    ++pass;
+    // launches of the pass: reset and summary, per class 3 + the loop trips
+    int64_t nl = 2;
+    for (int k = 0; k < f.n_classes; ++k)
+      nl += 3 + (int64_t)F->h_out[1 + k] * kIterationLaunches;
+    c->launches += nl;
+    if (pass_gain) pass_gain[pass - 1] = F->h_out[0];
+    if (!(F->h_out[0] > pass_tol * f.n_region)) break;
+  }
+  if (passes_out) *passes_out = pass;
+  return CELESTE_OK;
+}
+
+int celeste_fit_results(celeste_ctx* c, const celeste_fit* F, int32_t* status, int32_t* iters,
+                        int32_t* accepted, double* delta) {
+  if (!c || !F || F->ctx != c) return CELESTE_EINVAL;
+  const size_t S = (size_t)F->n_sources;
+  const FitView& f = F->f;
+  if (status) CK(cudaMemcpyAsync(status, f.status, S * 4, cudaMemcpyDeviceToDevice, c->stream));
+  if (iters) CK(cudaMemcpyAsync(iters, f.iters_total, S * 4, cudaMemcpyDeviceToDevice, c->stream));
+  if (accepted) CK(cudaMemcpyAsync(accepted, f.accepted, S * 4, cudaMemcpyDeviceToDevice, c->stream));
+  if (delta) CK(cudaMemcpyAsync(delta, f.delta, S * 8, cudaMemcpyDeviceToDevice, c->stream));
+  return CELESTE_OK;
 }
 
 }  // extern "C"

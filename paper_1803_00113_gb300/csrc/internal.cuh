@@ -152,6 +152,27 @@ cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const 
                                  const double* delta, double* p, double* pred);
 cudaError_t launch_mark_active(const Launch& L, const PlanView& v, const int32_t* status);
 
+// fit.cu: the region fit's per-source state (device arrays indexed by source
+// id unless noted) and its bookkeeping kernels.
+constexpr double kDelta0 = 1.0;   // initial trust radius of a subsolver call
+struct FitView {
+  const int32_t* region;   // [n_region] source ids of the region
+  double* delta;
+  int32_t* status;
+  int32_t* iters_pass;     // Newton iterations in the current pass
+  int32_t* iters_total;    // over all passes
+  int32_t* accepted;       // accepted steps over all passes
+  uint8_t* done;           // retired for the rest of the pass
+  double* gain;            // summed actual gain of accepted steps this pass
+  int32_t* class_iter;     // [n_classes] loop trips of each class this pass
+  double* out;             // [1 + n_classes] pass summary
+  int32_t n_region, n_classes, max_iter;
+};
+cudaError_t launch_fit_reset(cudaStream_t stream, const FitView& f);
+cudaError_t launch_fit_check(cudaStream_t stream, const PlanView& v, const FitView& f,
+                             const double* rel_trial, int cls, cudaGraphConditionalHandle h);
+cudaError_t launch_fit_pass_end(cudaStream_t stream, const FitView& f);
+
 // ---- small device helpers ----------------------------------------------
 __device__ __forceinline__ void set_error(unsigned int* err, unsigned int bit) {
   atomicOr(err, bit);

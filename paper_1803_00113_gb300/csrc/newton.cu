@@ -521,7 +521,8 @@ __global__ void mark_active_kernel(PlanView v, const int32_t* status) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= v.n) return;
   const int st = status[v.src_ids[j]];
-  v.active[j] = (st == CELESTE_ST_CONVERGED || st == CELESTE_ST_FAILED) ? 0 : 1;
+  v.active[j] =
+      (st == CELESTE_ST_CONVERGED || st == CELESTE_ST_FAILED || st == CELESTE_ST_MAXITER) ? 0 : 1;
 }
 
 static bool g_attr_set = false;

@@ -100,3 +100,28 @@ def test_hessian_vector_products(cel):
         sc = oracle.abs_sum_scales(p, s)
         scale = np.maximum(np.abs(ref["hess"]), sc["hess"]) @ np.abs(vv[j])
         assert np.all(np.abs(hv[j] - ref["hess"] @ vv[j]) <= TOL * scale), j
+
+
+def test_kernel_timing_by_kind(cel):
+    p = fields.batched(seed=34, n_sources=5, min_side=15, max_side=31, max_images_per_band=2,
+                       max_neighbours=2)
+    ctx = cel.Context(p.model)
+    dp = cel.DeviceProblem(p)
+    plan = cel.Plan(ctx, dp, list(range(p.n_sources)))
+    ctx.profile(True, kinds="all")
+    cel.elbo_grad_hess(plan)
+    cel.elbo_grad(plan)
+    cel.elbo(plan)
+    t = ctx.profile_kernels(reset=True)
+    assert t["background"][1] == 3 and t["derivs"][1] == 1 and t["grad"][1] == 1
+    assert t["value"][1] == 1 and t["epilogue"][1] == 3 and t["tr_step"][1] == 0
+    for k in ("derivs", "grad", "value", "background"):
+        assert t[k][0] > 0 and t[k][2] == t[k][1] * plan.visits
+    # derivative kernel only: the other kinds run untimed
+    ctx.profile(True)
+    delta, status = cel.newton_state(dp)
+    cel.newton_step(plan, delta, status)
+    t = ctx.profile_kernels(reset=True)
+    assert t["derivs"][1] == 1 and sum(v[1] for v in t.values()) == 1
+    assert ctx.profile_read(reset=True)[1] == 0
+    ctx.profile(False)
