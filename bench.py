@@ -51,9 +51,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["field", "batched"], default="field")
+    ap.add_argument("--workload", choices=["field", "batched", "serving"], default="field")
+    ap.add_argument("--rates", default="50,200,500,1000,2000",
+                    help="serving: Poisson arrival rates (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="serving: arrival window per rate")
+    ap.add_argument("--pool", type=int, default=96, help="serving: distinct requests generated")
     ap.add_argument("--sources", type=int, default=0, help="override the source count")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cache", action="store_true",
+                    help="re-render neighbours for every background instead of caching renders")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -229,7 +236,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         ctx = cel.Context(problem.model, device=local, stream=stream)
-        dp = cel.DeviceProblem(problem, dev)
+        # cache renders where neighbours are dense (blends); in a sparse
+        # field re-rendering the few neighbours is cheaper than the cache
+        dense = problem.nbr_ptr[-1] >= 1.5 * problem.n_sources
+        dp = cel.DeviceProblem(problem, dev, render_cache=dense and not args.no_cache)
         classes = cel.color_classes(problem)
         tiles = None
         if args.autotune or args.workload == "batched":
@@ -249,6 +259,11 @@ def run_ours(args):
             status.copy_(status0)
 
         def step():
+            # the cache follows theta: render every source at the reset point,
+            # then each class's step refreshes the sources it moved
+            if dp.cache is not None:
+                for p in plans:
+                    cel.render_cache(p)
             for p in plans:
                 cel.newton_step(p, delta, status)
 
@@ -309,7 +324,7 @@ def run_ours(args):
         n_launch = ctx.launches() - l0
         if graph is not None:
             # a replay launches the captured kernels: count them per step
-            n_launch = (ctx.launches() - l0) + args.steps * launches_per_step(plans)
+            n_launch = (ctx.launches() - l0) + args.steps * launches_per_step(plans, dp.cache is not None)
         clk = clocks.stop()
         step_ms = [a.elapsed_time(b) for a, b in ev]
         ctx.synchronize()
@@ -423,7 +438,8 @@ def run_ours(args):
         "config": dict(cfg, l2="flushed between steps (256 MB write outside the timed events)",
                        graph=graph is not None, visits_per_step=visits,
                        colour_classes=len(classes),
-                       tiles_per_area_bucket=tiles or [256, 256, 256, 256]),
+                       tiles_per_area_bucket=tiles or [256, 256, 256, 256],
+                       render_cache=dp.cache is not None),
         "grad_vs_hess": ratio,
         "kernels_one_step": breakdown,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -450,20 +466,53 @@ def run_ours(args):
     return line
 
 
-def launches_per_step(plans):
+def launches_per_step(plans, cache):
     # per plan and Newton iteration: mark, setup, background, derivatives,
-    # epilogue, trust-region step, trial setup, trial value, trial epilogue, accept
-    return 10 * len(plans)
+    # epilogue, trust-region step, trial setup, trial value, trial epilogue,
+    # accept; with the render cache also the setup and render of every plan
+    # at the start of the step and the commit after the accept
+    return (13 if cache else 10) * len(plans)
 
 
 # ---------------------------------------------------------------------------
 # the reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
+def run_reference_serving(args):
+    """The oracle's region fit on single-source requests of the serving
+    pool (the smallest requests; a bounded sample)."""
+    import torch
+    from oracle import newton as ON
+    times = []
+    k = 0
+    for i in range(args.warmup + args.steps):
+        q = fields.region_request(SEED + 5 + k, n_sources=1, side=32)
+        k += 1
+        t0 = time.perf_counter()
+        ON.region_fit(q, max_passes=5, max_iter=50, pass_tol=1e-3)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = len(times) / sum(times)
+    sample = (f"each step: FP64 oracle region fit of one 1-source, 32x32 px request "
+              f"({args.steps} steps)")
+    return {"impl": "reference", "metric": "region fits/s (Poisson arrivals, result back on the host)",
+            "value": value, "unit": "fits/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded region requests)",
+            "config": {"workload": "serving (oracle: smallest requests, one at a time)"},
+            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args):
     world, rank, local = dist_info()
     if rank != 0:
         return None
+    if args.workload == "serving":
+        return run_reference_serving(args)
     import torch
     import oracle
     problem, cfg = workload(args.workload, args.sources, SEED + 1)
@@ -496,9 +545,114 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------
+# serving: region fits submitted at Poisson arrival times
+# ---------------------------------------------------------------------------
+
+def _serve_run(cel, srv, pool, arrivals):
+    """Submits pool requests (cycled) at the given arrival times; returns the
+    per-request results (latency measured natively, submit -> ready)."""
+    tickets = []
+    t0 = time.perf_counter()
+    for k, at in enumerate(arrivals):
+        while True:
+            dt = at - (time.perf_counter() - t0)
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 2e-3) if dt > 2e-3 else 0)
+        while True:
+            try:
+                tickets.append(srv.submit(pool[k % len(pool)]))
+                break
+            except cel.CelesteError as e:
+                if getattr(e, "code", 0) != cel.EAGAIN:
+                    raise
+                time.sleep(1e-3)
+    out = []
+    for t in tickets:
+        r = None
+        while r is None:
+            r = srv.poll(t, wait_ms=200)
+        if r["code"] != 0:
+            raise RuntimeError(f"request failed with code {r['code']}")
+        out.append(r)
+    wall = time.perf_counter() - t0
+    return out, wall
+
+
+def run_serving(args):
+    import torch
+    world, rank, local = dist_info()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    from paper_1803_00113_gb300 import build_lib
+    build_lib.build()
+    from paper_1803_00113_gb300 import celeste as cel
+    reqs = [fields.region_request(SEED + 5 + k) for k in range(args.pool)]
+    pool = [cel.Server.prepare(q) for q in reqs]
+    model = reqs[0].model
+    mean_in = float(np.mean([q.bytes_in for q in pool]))
+    mean_out = float(np.mean([q.n_sources * (27 * 8 + 4) for q in reqs]))
+    rng = np.random.default_rng(SEED + 5)
+    rates = [float(r) for r in args.rates.split(",")]
+
+    def arrivals(rate, n):
+        return np.cumsum(rng.exponential(1.0 / rate, n))
+
+    srv = cel.Server(model, device=local)
+    _serve_run(cel, srv, pool[:8], np.zeros(8))          # warm-up: graphs, buffers
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_rate = {}
+    for rate in rates:
+        n = max(int(rate * args.serve_seconds), 20)
+        res, wall = _serve_run(cel, srv, pool, arrivals(rate, n))
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        per_rate[str(int(rate))] = {
+            "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "throughput": n / wall,
+            "mean_batch": float(np.mean([r["batch_requests"] for r in res])),
+            "mean_passes": float(np.mean([r["passes"] for r in res]))}
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    # the plain form: one request at a time, each its own fit, saturated
+    plain_srv = cel.Server(model, device=local, workers=1, max_batch=1)
+    _serve_run(cel, plain_srv, pool[:4], np.zeros(4))
+    n_plain = min(len(pool), 48)
+    res, wall = _serve_run(cel, plain_srv, pool[:n_plain], np.zeros(n_plain))
+    plain_srv.close()
+    plain = {"throughput": n_plain / wall,
+             "p50_ms_saturated": float(np.percentile([r["latency_s"] * 1e3 for r in res], 50)),
+             "form": "one request per fit, one request in flight (saturated queue)"}
+    best = max(per_rate.values(), key=lambda d: d["throughput"])
+    top = per_rate[str(int(rates[-1]))]
+    return {"metric": "region fits/s (Poisson arrivals, result back on the host)",
+            "value": best["throughput"], "unit": "fits/s", "n_gpus": 1,
+            "steps": len(rates), "warmup": 1, "ms_per_step": top["p50_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded region requests: 1..64 sources, 32..512 px, 5 bands, "
+                    "1..4 images per band)",
+            "config": {"workload": "serving: Poisson arrivals at "
+                                   f"{args.rates} requests/s, {args.serve_seconds:g} s each, "
+                                   f"fits of <= 5 passes x <= 50 Newton iterations",
+                       "pool": args.pool, "l2": "inputs stream in per request (not reused)"},
+            "latency": per_rate,
+            "plain_per_request": plain, "vs_plain": best["throughput"] / plain["throughput"],
+            "e2e": {"value": best["throughput"], "unit": "fits/s",
+                    "h2d_bytes_per_step": int(mean_in), "d2h_bytes_per_step": int(mean_out)},
+            "gpu_launches": int(st["launches"]), "clocks": clk}
+
+
 def main(argv=None):
     args = parse_args(argv)
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "serving":
+        line = run_serving(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
     world = dist_info()[0]

@@ -621,3 +621,42 @@ def batched(seed: int = 1803_00113 + 3, n_sources=8192, min_side=15, max_side=10
     truth["pos"] = pos_all
     return b.finish(rng, truth, f"batched, {n_sources} sources, patches {min_side}..{max_side} px, "
                     f"1..{max_images_per_band} images per band, 0..{max_neighbours} neighbours", {})
+
+
+def region_request(seed: int, n_sources: Optional[int] = None, side: Optional[int] = None,
+                   max_images_per_band=4, max_sources=64, min_region=32, max_region=512,
+                   model: Optional[Model] = None, star_frac=0.3):
+    """One serving request: a square sky region and the sources inside it.
+
+    Unless given, the source count is log-uniform on [1, max_sources] and the
+    region side log-uniform on [min_region, max_region] px; every band has a
+    uniform number of exposures in 1..max_images_per_band, each with its own
+    PSF, constant sky, calibration and WCS jitter.  Sources sit at uniform
+    positions; patches follow the field's rule (odd side where the source
+    exceeds 0.2 sqrt(sky), clamped to [15, 101] and to the region).
+    """
+    rng = np.random.default_rng(seed)
+    model = model or make_model()
+    if n_sources is None:
+        n_sources = int(round(math.exp(rng.uniform(0.0, math.log(max_sources)))))
+    if side is None:
+        side = int(round(math.exp(rng.uniform(math.log(min_region), math.log(max_region)))))
+    b = _Builder(model)
+    truth = _draw_truth(rng, model, star_frac, n_sources)
+    pos = rng.uniform(3.0, side - 4.0, (n_sources, 2))
+    imgs = []
+    for band in range(N_BANDS):
+        for _ in range(int(rng.integers(1, max_images_per_band + 1))):
+            A, t = _draw_wcs(rng)
+            imgs.append(b.add_image(band, side, side, np.full((1, 1), rng.uniform(50, 200)),
+                                    200.0 * rng.uniform(0.9, 1.1), A, t, _draw_psf(rng)))
+    for s in range(n_sources):
+        ps = _patch_side(truth, s, 50.0, 220.0)
+        rects = [_rect_for(b, n, pos[s], ps) for n in imgs]
+        _render_truth_images(b, imgs, truth, s, pos[s], rects)
+        b.patches.append([(n,) + r for n, r in zip(imgs, rects)])
+    _link_neighbours(b, 0, n_sources)
+    b.theta.extend(_init_theta(rng, truth, pos, n_sources).ravel())
+    truth["pos"] = pos
+    return b.finish(rng, truth, f"region {side}x{side} px, {n_sources} sources, "
+                    f"1..{max_images_per_band} images per band", dict(side=side))

@@ -141,6 +141,14 @@ typedef struct celeste_problem {
   const int32_t* h_nbr_idx;
   int64_t n_pixels, n_sky, n_pool;
   int32_t n_images, n_sources, n_patches, n_nbr;
+  /* Optional (may be NULL): float2 (E, V) of each source's own moments at
+   * each of its patch pixels, in the patch-pool layout ([n_pool] pairs at
+   * each patch's pool_offset).  With it, neighbour backgrounds are gathered
+   * from the cache instead of re-rendering every neighbour (the same values,
+   * bit for bit).  celeste_newton_step re-renders the sources whose step
+   * was accepted and celeste_fit_run keeps it current; after changing theta
+   * any other way, refresh it with celeste_render_cache. */
+  float* render_cache;
 } celeste_problem;
 
 /* Tile shape of the pixel kernels: the number of pixels one warp reduces
@@ -192,7 +200,8 @@ int celeste_profile_read(celeste_ctx* ctx, int reset, double* total_ms, int64_t*
 #define CELESTE_K_EPILOGUE    5
 #define CELESTE_K_TRSTEP      6
 #define CELESTE_K_OTHER       7
-#define CELESTE_K_COUNT       8
+#define CELESTE_K_RENDER      8   /* render-cache refresh */
+#define CELESTE_K_COUNT       9
 int celeste_profile_kernels(celeste_ctx* ctx, int reset, double* ms, int64_t* launches,
                             int64_t* visits);
 
@@ -238,7 +247,9 @@ int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, doubl
  * status[n_sources] (device, indexed by source id) carry the state between
  * calls; initialise delta to 1 and status to 0.  Status values:
  * CELESTE_ST_*.  elbo_rel (device [n], plan order, may be NULL) receives
- * L_s - L_s(absent) at the iterate before the step. */
+ * L_s - L_s(absent) at the iterate before the step.  A trial point whose
+ * value is not finite (an FP32 overflow far from the iterate) is rejected
+ * like any other failed step and raises no device error. */
 #define CELESTE_ST_ACCEPTED   0
 #define CELESTE_ST_REJECTED   1
 #define CELESTE_ST_CONVERGED  2
@@ -281,6 +292,80 @@ int celeste_fit_run(celeste_ctx* ctx, celeste_fit* fit, int32_t max_passes, int3
 int celeste_fit_results(celeste_ctx* ctx, const celeste_fit* fit, int32_t* status,
                         int32_t* iters, int32_t* accepted, double* delta);
 
+/* ---- serving (region fits submitted by independent callers) ------------
+ *
+ * A server owns worker threads, each with its own context, stream and
+ * resident device buffers.  celeste_submit validates a region request,
+ * copies it (the caller's buffers may be reused as soon as it returns) and
+ * queues it; a worker takes every queued request that fits its device
+ * budget (device_bytes, estimated per request from its pixels, patches and
+ * sources), lays them out as one problem and runs one fit over it in which
+ * each request is a segment with its own passes and stopping rule (as
+ * celeste_fit_run: max_passes, max_iter, pass_tol), so a request's result is
+ * the same whether it ran alone or batched.  celeste_poll returns the result
+ * once the request's segment has stopped.
+ *
+ * Errors: celeste_submit returns CELESTE_EINVAL for a malformed request
+ * (sizes, offsets, a patch outside its image, a neighbour index out of
+ * range), CELESTE_ETOOLARGE when the request alone exceeds device_bytes,
+ * CELESTE_EAGAIN when the queued requests already hold queue_bytes.
+ * celeste_poll returns CELESTE_EBUSY until the request is done (waiting up
+ * to wait_ms for it), CELESTE_ENOTFOUND for an unknown or already collected
+ * ticket, and otherwise the request's outcome (CELESTE_OK, or the error of
+ * its batch, e.g. CELESTE_EDEVICE when a device error bit was raised). */
+typedef struct celeste_server_config {
+  int32_t workers;          /* worker threads (0 = 2) */
+  int32_t max_batch;        /* requests per batch (0 = no limit) */
+  int64_t device_bytes;     /* per-worker budget of resident request data (0 = 4 GiB) */
+  int64_t queue_bytes;      /* admission limit of queued requests (0 = 4 x budget x workers) */
+  int32_t max_passes;       /* fit limits (0 = 5, 50) */
+  int32_t max_iter;
+  double pass_tol;          /* nats per source */
+  int32_t start_paused;     /* workers take no batch until celeste_server_pause(s, 0) */
+  int32_t reserved;
+} celeste_server_config;
+
+/* One region: HOST arrays laid out as in celeste_problem (offsets, patch
+ * and neighbour indices local to the request). */
+typedef struct celeste_region_request {
+  const float* pixels;
+  const float* sky;
+  const celeste_image* images;
+  const double* theta;             /* [n_sources][27] initial values */
+  const int32_t* patch_ptr;        /* [n_sources + 1] */
+  const celeste_patch* patches;
+  const int32_t* nbr_ptr;          /* [n_sources + 1] */
+  const int32_t* nbr_idx;
+  int64_t n_pixels, n_sky;
+  int32_t n_images, n_sources, n_patches, n_nbr;
+} celeste_region_request;
+
+typedef struct celeste_request_info {
+  int32_t n_sources;
+  int32_t passes;               /* passes the request's fit ran */
+  int32_t batch_requests;       /* requests in the batch it ran in */
+  uint32_t device_error;        /* device error word of its batch (CELESTE_DERR_*) */
+  double last_pass_gain;        /* ELBO gain of its last pass */
+  double queue_s;               /* submit -> taken by a worker */
+  double latency_s;             /* submit -> result ready */
+} celeste_request_info;
+
+typedef struct celeste_server celeste_server;
+int celeste_server_create(const celeste_model* model, int device,
+                          const celeste_server_config* config, celeste_server** out);
+/* Stops the workers after their current batch; queued requests are dropped. */
+int celeste_server_destroy(celeste_server* server);
+int celeste_server_pause(celeste_server* server, int paused);
+int celeste_submit(celeste_server* server, const celeste_region_request* request,
+                   uint64_t* ticket);
+/* theta_out (HOST [n_sources][27]) and status_out (HOST [n_sources],
+ * CELESTE_ST_* of each source's last subsolver call) may be NULL.  A
+ * collected ticket is forgotten. */
+int celeste_poll(celeste_server* server, uint64_t ticket, int32_t wait_ms, double* theta_out,
+                 int32_t* status_out, celeste_request_info* info);
+/* Kernel launches and batches so far; returns the first worker error. */
+int celeste_server_stats(celeste_server* server, int64_t* launches, int64_t* batches);
+
 /* Only the FP64 trust-region subproblem, for n independent problems:
  * maximise g.p + p.H.p/2 subject to |p| <= delta (Sec. 4.3).  g[n][27],
  * H[n][27][27], delta[n] in; p[n][27], pred[n] (= g.p + p.H.p/2) out; all
@@ -292,6 +377,9 @@ int celeste_tr_subproblem(celeste_ctx* ctx, int32_t n, const double* g, const do
  * every plan source, the source's own E_q[l f] and V_q[l f] at each patch
  * pixel, written to E_out/V_out at the patch's pool_offset (row major). */
 int celeste_render(celeste_ctx* ctx, const celeste_plan* plan, float* E_out, float* V_out);
+/* Renders the plan's sources at theta into problem->render_cache (no-op
+ * when the problem has none). */
+int celeste_render_cache(celeste_ctx* ctx, const celeste_plan* plan);
 /* Sky plus the moments of the neighbours at each patch pixel of every
  * plan source (the background a source is fitted against). */
 int celeste_background(celeste_ctx* ctx, const celeste_plan* plan, float* bgE_out, float* bgV_out);

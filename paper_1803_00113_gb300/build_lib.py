@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(OUT_DIR, "libceleste.so")
-SOURCES = ["setup.cu", "pixel.cu", "epilogue.cu", "newton.cu", "fit.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "pixel.cu", "epilogue.cu", "newton.cu", "fit.cu", "serve.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          f"-I{INCLUDE}"]
@@ -67,7 +67,7 @@ def build(force=False, verbose=False):
         for (obj, log), src in zip(results, SOURCES):
             sys.stderr.write(f"== {src}\n{log}")
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

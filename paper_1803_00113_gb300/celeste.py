@@ -41,13 +41,37 @@ class _Model(ctypes.Structure):
                 ("e_profile", ctypes.c_double * 2), ("e_axis", ctypes.c_double * 2)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("queue_bytes", ctypes.c_int64),
+                ("max_passes", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("pass_tol", ctypes.c_double), ("start_paused", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("pixels", "sky", "images", "theta", "patch_ptr",
+                                                 "patches", "nbr_ptr", "nbr_idx")] + \
+               [("n_pixels", ctypes.c_int64), ("n_sky", ctypes.c_int64),
+                ("n_images", ctypes.c_int32), ("n_sources", ctypes.c_int32),
+                ("n_patches", ctypes.c_int32), ("n_nbr", ctypes.c_int32)]
+
+
+class _RequestInfo(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("batch_requests", ctypes.c_int32), ("device_error", ctypes.c_uint32),
+                ("last_pass_gain", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
 class _Problem(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in (
         "pixels", "sky", "images", "theta", "patch_ptr", "patches", "nbr_ptr", "nbr_idx",
         "h_patch_ptr", "h_patches", "h_images", "h_nbr_ptr", "h_nbr_idx")] + [
         ("n_pixels", ctypes.c_int64), ("n_sky", ctypes.c_int64), ("n_pool", ctypes.c_int64),
         ("n_images", ctypes.c_int32), ("n_sources", ctypes.c_int32),
-        ("n_patches", ctypes.c_int32), ("n_nbr", ctypes.c_int32)]
+        ("n_patches", ctypes.c_int32), ("n_nbr", ctypes.c_int32),
+        ("render_cache", ctypes.c_void_p)]
 
 
 class _Tuning(ctypes.Structure):
@@ -90,6 +114,7 @@ def lib():
         "celeste_tr_subproblem": (ctypes.c_int, [P, I32, P, P, P, P, P]),
         "celeste_render": (ctypes.c_int, [P, P, P, P]),
         "celeste_background": (ctypes.c_int, [P, P, P, P]),
+        "celeste_render_cache": (ctypes.c_int, [P, P]),
         "celeste_color_sources": (ctypes.c_int, [I32, P, P, P]),
         "celeste_fit_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem), P, I32,
                                               ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
@@ -97,6 +122,15 @@ def lib():
         "celeste_fit_classes": (ctypes.c_int, [P]),
         "celeste_fit_run": (ctypes.c_int, [P, P, I32, I32, D, ctypes.POINTER(I32), P]),
         "celeste_fit_results": (ctypes.c_int, [P, P, P, P, P, P]),
+        "celeste_server_create": (ctypes.c_int, [ctypes.POINTER(_Model), ctypes.c_int,
+                                                 ctypes.POINTER(_ServerConfig), ctypes.POINTER(P)]),
+        "celeste_server_destroy": (ctypes.c_int, [P]),
+        "celeste_server_pause": (ctypes.c_int, [P, ctypes.c_int]),
+        "celeste_submit": (ctypes.c_int, [P, ctypes.POINTER(_Request),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+        "celeste_poll": (ctypes.c_int, [P, ctypes.c_uint64, I32, P, P,
+                                        ctypes.POINTER(_RequestInfo)]),
+        "celeste_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "celeste_elbo_grad_hess_noalloc": (ctypes.c_int, [ctypes.POINTER(_Model),
                                                           ctypes.POINTER(_Problem), P, I32, P,
                                                           P, P, P, P, P]),
@@ -116,12 +150,16 @@ def exported_symbols():
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
             "celeste_elbo_grad_hess", "celeste_elbo", "celeste_elbo_grad", "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
+            "celeste_render_cache",
             "celeste_color_sources", "celeste_fit_create", "celeste_fit_destroy",
             "celeste_fit_classes", "celeste_fit_run", "celeste_fit_results",
+            "celeste_server_create", "celeste_server_destroy", "celeste_server_pause",
+            "celeste_submit", "celeste_poll", "celeste_server_stats",
             "celeste_elbo_grad_hess_noalloc"]
 
 
-KERNEL_KINDS = ("setup", "background", "derivs", "grad", "value", "epilogue", "tr_step", "other")
+KERNEL_KINDS = ("setup", "background", "derivs", "grad", "value", "epilogue", "tr_step", "other",
+                "render")
 
 
 class CelesteError(RuntimeError):
@@ -234,35 +272,41 @@ class Context:
             pass
 
 
+def _host_structs(p):
+    """Image and patch struct arrays of a fields.Problem, in the C layouts."""
+    img = np.zeros(p.n_images, dtype=IMAGE_DTYPE)
+    img["pix_offset"] = p.img_pix_off
+    img["sky_offset"] = p.img_sky_off
+    img["band"] = p.img_band
+    img["height"] = p.img_h
+    img["width"] = p.img_w
+    img["row_stride"] = p.img_stride
+    img["sky_ny"] = p.img_sky_ny
+    img["sky_nx"] = p.img_sky_nx
+    img["calib"] = p.img_calib
+    img["wcs_A"] = p.img_A.reshape(-1, 4)
+    img["wcs_t"] = p.img_t
+    img["psf"] = p.img_psf
+    pat = np.zeros(p.n_patches, dtype=PATCH_DTYPE)
+    pat["image"] = p.patch_img
+    pat["x0"] = p.patch_x0
+    pat["y0"] = p.patch_y0
+    pat["w"] = p.patch_w
+    pat["h"] = p.patch_h
+    area = p.patch_w.astype(np.int64) * p.patch_h.astype(np.int64)
+    pat["pool_offset"] = np.concatenate([[0], np.cumsum(area)[:-1]]) if len(area) else []
+    return img, pat, int(area.sum())
+
+
 class DeviceProblem:
     """A fields.Problem uploaded to the device (plus the host index copies)."""
 
-    def __init__(self, problem, device=None):
+    def __init__(self, problem, device=None, render_cache: bool = False):
         dev = device or torch.device("cuda", 0)
         self.host = problem
         p = problem
-        img = np.zeros(p.n_images, dtype=IMAGE_DTYPE)
-        img["pix_offset"] = p.img_pix_off
-        img["sky_offset"] = p.img_sky_off
-        img["band"] = p.img_band
-        img["height"] = p.img_h
-        img["width"] = p.img_w
-        img["row_stride"] = p.img_stride
-        img["sky_ny"] = p.img_sky_ny
-        img["sky_nx"] = p.img_sky_nx
-        img["calib"] = p.img_calib
-        img["wcs_A"] = p.img_A.reshape(-1, 4)
-        img["wcs_t"] = p.img_t
-        img["psf"] = p.img_psf
-        pat = np.zeros(p.n_patches, dtype=PATCH_DTYPE)
-        pat["image"] = p.patch_img
-        pat["x0"] = p.patch_x0
-        pat["y0"] = p.patch_y0
-        pat["w"] = p.patch_w
-        pat["h"] = p.patch_h
-        area = p.patch_w.astype(np.int64) * p.patch_h.astype(np.int64)
-        pat["pool_offset"] = np.concatenate([[0], np.cumsum(area)[:-1]]) if len(area) else []
-        self.n_pool = int(area.sum())
+        img, pat, n_pool = _host_structs(p)
+        self.n_pool = n_pool
         self.pool_offset = pat["pool_offset"].copy()
         self.h_images = img
         self.h_patches = pat
@@ -297,6 +341,10 @@ class DeviceProblem:
         s.n_pixels, s.n_sky, s.n_pool = p.pixels.size, p.sky.size, self.n_pool
         s.n_images, s.n_sources, s.n_patches = p.n_images, p.n_sources, p.n_patches
         s.n_nbr = int(p.nbr_idx.size)
+        # (E, V) of every source at each of its patch pixels, pool layout
+        self.cache = (torch.zeros(2 * max(self.n_pool, 1), dtype=torch.float32, device=dev)
+                      if render_cache else None)
+        s.render_cache = self.cache.data_ptr() if render_cache else None
         self.struct = s
 
     @property
@@ -409,6 +457,11 @@ def render(plan: Plan):
     return E, V
 
 
+def render_cache(plan: Plan):
+    """Refreshes the problem's render cache for the plan's sources."""
+    _check(lib().celeste_render_cache(plan.ctx.handle, plan.handle), "celeste_render_cache")
+
+
 def background(plan: Plan):
     dev = plan.ctx.device
     E = torch.zeros(plan.dprob.n_pool, dtype=torch.float32, device=dev)
@@ -477,6 +530,101 @@ class Fit:
     def close(self):
         if getattr(self, "handle", None):
             lib().celeste_fit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+EAGAIN, EBUSY, ENOTFOUND, ETOOLARGE = -5, -6, -7, -8
+
+
+class Server:
+    """Region fits submitted as independent requests (celeste_server_*)."""
+
+    def __init__(self, model, device: int = 0, workers: int = 2, max_batch: int = 0,
+                 device_bytes: int = 0, queue_bytes: int = 0, max_passes: int = 5,
+                 max_iter: int = 50, pass_tol: float = 1e-3, start_paused: bool = False):
+        if not torch.cuda.is_available():
+            raise CelesteError("no CUDA device: the library has no CPU path")
+        self.model_struct = model_struct(model)
+        cfg = _ServerConfig(workers, max_batch, device_bytes, queue_bytes, max_passes, max_iter,
+                            pass_tol, 1 if start_paused else 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().celeste_server_create(ctypes.byref(self.model_struct), device,
+                                           ctypes.byref(cfg), ctypes.byref(h)),
+               "celeste_server_create")
+        self.handle = h
+        self.sizes = {}
+
+    def pause(self, paused: bool = True):
+        _check(lib().celeste_server_pause(self.handle, 1 if paused else 0), "celeste_server_pause")
+
+    @staticmethod
+    def prepare(problem):
+        """The C request of a fields.Problem (arrays kept alive with it)."""
+        img, pat, _ = _host_structs(problem)
+        arrs = dict(pixels=np.ascontiguousarray(problem.pixels, dtype=np.float32),
+                    sky=np.ascontiguousarray(problem.sky, dtype=np.float32),
+                    images=img, theta=np.ascontiguousarray(problem.theta, dtype=np.float64),
+                    patch_ptr=np.ascontiguousarray(problem.patch_ptr, dtype=np.int32),
+                    patches=pat,
+                    nbr_ptr=np.ascontiguousarray(problem.nbr_ptr, dtype=np.int32),
+                    nbr_idx=np.ascontiguousarray(problem.nbr_idx if len(problem.nbr_idx)
+                                                 else np.zeros(1), dtype=np.int32))
+        q = _Request(*[arrs[k].ctypes.data for k in ("pixels", "sky", "images", "theta",
+                                                    "patch_ptr", "patches", "nbr_ptr", "nbr_idx")],
+                     problem.pixels.size, problem.sky.size, problem.n_images, problem.n_sources,
+                     problem.n_patches, int(len(problem.nbr_idx)))
+        q._arrays = arrs
+        q.bytes_in = sum(a.nbytes for a in arrs.values())
+        return q
+
+    def submit(self, problem) -> int:
+        """Queues a fields.Problem (or a prepared request) as one region;
+        returns its ticket (raises CelesteError with .code EAGAIN when the
+        queue is full)."""
+        q = problem if isinstance(problem, _Request) else self.prepare(problem)
+        t = ctypes.c_uint64(0)
+        rc = lib().celeste_submit(self.handle, ctypes.byref(q), ctypes.byref(t))
+        if rc < 0:
+            err = CelesteError(f"celeste_submit failed with code {rc}")
+            err.code = rc
+            raise err
+        self.sizes[t.value] = q.n_sources
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """None while the request runs; else a dict with theta [n, 27],
+        status [n], passes, latency_s, queue_s, batch_requests and code."""
+        if ticket not in self.sizes:
+            raise CelesteError(f"unknown ticket {ticket}")
+        n = self.sizes[ticket]
+        theta = np.zeros((n, N_THETA), dtype=np.float64)
+        status = np.zeros(n, dtype=np.int32)
+        info = _RequestInfo()
+        rc = lib().celeste_poll(self.handle, ticket, int(wait_ms), theta.ctypes.data,
+                                status.ctypes.data, ctypes.byref(info))
+        if rc == EBUSY:
+            return None
+        if rc == ENOTFOUND or ticket not in self.sizes:
+            raise CelesteError(f"unknown ticket {ticket}")
+        del self.sizes[ticket]
+        return dict(theta=theta, status=status, passes=info.passes, latency_s=info.latency_s,
+                    queue_s=info.queue_s, batch_requests=info.batch_requests,
+                    last_pass_gain=info.last_pass_gain, device_error=info.device_error, code=rc)
+
+    def stats(self):
+        nl, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = lib().celeste_server_stats(self.handle, ctypes.byref(nl), ctypes.byref(nb))
+        return dict(launches=nl.value, batches=nb.value, worker_error=rc)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

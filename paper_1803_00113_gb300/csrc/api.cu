@@ -9,61 +9,11 @@
 #include <unordered_map>
 #include <vector>
 
-#include "internal.cuh"
+#include "host.h"
 
 using namespace celeste;
 
-struct celeste_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int sm_count = 0;
-  ModelDev* d_model = nullptr;
-  unsigned int* d_err = nullptr;
-  int n_exp = 0, n_dev = 0;
-  int64_t launches = 0;
-  // event timing of kernel launches by kind (celeste_profile_*)
-  unsigned profiling = 0;            // bit k: time kernels of kind k
-  std::vector<cudaEvent_t> events;   // start/stop pairs, reused
-  std::vector<int> kinds;            // kind of pair k
-  std::vector<int64_t> visits;       // visits of pair k (pixel kernels)
-  size_t n_timed = 0;                // pairs recorded since the last reset
-};
-
-struct celeste_plan {
-  celeste_ctx* ctx = nullptr;
-  PlanView v{};
-  const celeste_patch* d_patches = nullptr;
-  double* rel_trial = nullptr;
-  std::vector<void*> allocs;
-  int64_t visits = 0;
-  celeste_tuning tuning{};
-};
-
-struct celeste_fit {
-  celeste_ctx* ctx = nullptr;
-  std::vector<int32_t> region;              // sorted source ids
-  std::vector<celeste_plan*> plans;         // one per colour class
-  std::vector<void*> allocs;
-  FitView f{};
-  double* h_out = nullptr;                  // pinned copy of f.out
-  cudaStream_t capture = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int built_max_iter = 0;
-  int n_sources = 0;
-};
-
-namespace {
-
-#define CK(call)                                \
-  do {                                          \
-    cudaError_t e_ = (call);                    \
-    if (e_ != cudaSuccess) return CELESTE_ECUDA; \
-  } while (0)
-
-int to_status(cudaError_t e) { return e == cudaSuccess ? CELESTE_OK : CELESTE_ECUDA; }
-
-Launch make_launch(const celeste_ctx* c, const celeste_plan* p) {
+Launch celeste::make_launch(const celeste_ctx* c, const celeste_plan* p) {
   Launch L;
   L.stream = c->stream;
   L.sm_count = c->sm_count;
@@ -74,6 +24,10 @@ Launch make_launch(const celeste_ctx* c, const celeste_plan* p) {
   L.n_dev = c->n_dev;
   return L;
 }
+
+namespace {
+
+int to_status(cudaError_t e) { return e == cudaSuccess ? CELESTE_OK : CELESTE_ECUDA; }
 
 // Inverse and log-determinant of a symmetric positive-definite 4x4 matrix
 // (Cholesky).  Returns false when it is not positive definite.
@@ -219,6 +173,24 @@ bool prepare_model(const celeste_model* m, ModelDev* md) {
 }
 
 }  // namespace celeste
+
+// One trust-region Newton iteration of the plan's active sources once the
+// neighbour records and background are in place: own records, derivative
+// pass, epilogue, FP64 step, trial records, trial value, accept.
+cudaError_t celeste::enqueue_iteration(celeste_ctx* c, celeste_plan* p, const Launch& L,
+                                     double* delta, int32_t* status) {
+  PlanView& v = p->v;
+  cudaError_t e = launch_mark_active(L, v, status);
+  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, false);
+  if (e == cudaSuccess) e = launch_pixels_derivs(L, v);
+  if (e == cudaSuccess) e = launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
+  if (e == cudaSuccess) e = launch_tr_step(L, v, delta, status);
+  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, true);
+  if (e == cudaSuccess) e = launch_pixels_value(L, v);
+  if (e == cudaSuccess) e = launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
+  if (e == cudaSuccess) e = launch_tr_accept(L, v, p->rel_trial, delta, status);
+  return e;
+}
 
 extern "C" {
 
@@ -436,6 +408,8 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   v.n_items = (int)items.size();
   v.n_bg = bg;
   v.err = c->d_err;
+  v.cache = reinterpret_cast<float2*>(pr->render_cache);
+  v.patches = pr->patches;
   p->d_patches = pr->patches;
   int32_t* d_ids = dev_alloc<int32_t>(p, n, &err);
   PairInfo* d_pairs = dev_alloc<PairInfo>(p, pairs.size(), &err);
@@ -444,6 +418,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   Item* d_items = dev_alloc<Item>(p, items.size(), &err);
   v.records = dev_alloc<float>(p, pairs.size() * (size_t)kRecF, &err);
   v.bg = dev_alloc<float2>(p, (size_t)bg, &err);
+  v.trial_render = pr->render_cache ? dev_alloc<float2>(p, (size_t)bg, &err) : nullptr;
   v.partials = dev_alloc<float>(p, items.size() * (size_t)kAcc, &err);
   v.vpartials = dev_alloc<float>(p, items.size() * 2, &err);
   v.theta_trial = dev_alloc<double>(p, (size_t)n * kTheta, &err);
@@ -549,25 +524,6 @@ int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* e
   }));
 }
 
-// One trust-region Newton iteration of the plan's active sources once the
-// neighbour records and background are in place: own records, derivative
-// pass, epilogue, FP64 step, trial records, trial value, accept.
-static cudaError_t enqueue_iteration(celeste_ctx* c, celeste_plan* p, const Launch& L,
-                                     double* delta, int32_t* status) {
-  PlanView& v = p->v;
-  cudaError_t e = launch_mark_active(L, v, status);
-  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, false);
-  if (e == cudaSuccess) e = launch_pixels_derivs(L, v);
-  if (e == cudaSuccess) e = launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
-  if (e == cudaSuccess) e = launch_tr_step(L, v, delta, status);
-  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, true);
-  if (e == cudaSuccess) e = launch_pixels_value(L, v);
-  if (e == cudaSuccess) e = launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
-  if (e == cudaSuccess) e = launch_tr_accept(L, v, p->rel_trial, delta, status);
-  return e;
-}
-constexpr int kIterationLaunches = 10;   // enqueue_iteration + fit_check
-
 int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, int32_t* status,
                         double* elbo_rel) {
   celeste_plan* p = const_cast<celeste_plan*>(pc);
@@ -591,13 +547,33 @@ int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, i
   rc = run_setup(c, p, 0, v.n_own_pairs, true);
   if (rc) return rc;
   c->launches += 3;
-  CK(timed(c, CELESTE_K_VALUE, p->visits, L.stream, [&] { return launch_pixels_value(L, v); }));
+  CK(timed(c, CELESTE_K_VALUE, p->visits, L.stream,
+           [&] { return launch_pixels_value(L, v, true); }));
   CK(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
     return launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
   }));
   CK(timed(c, CELESTE_K_OTHER, 0, L.stream,
            [&] { return launch_tr_accept(L, v, p->rel_trial, delta, status); }));
+  if (v.cache) {
+    // accepted sources: their trial render becomes their cached render
+    c->launches += 1;
+    CK(timed(c, CELESTE_K_RENDER, p->visits, L.stream,
+             [&] { return launch_commit_render(L, v, status); }));
+  }
   return CELESTE_OK;
+}
+
+int celeste_render_cache(celeste_ctx* c, const celeste_plan* pc) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c) return CELESTE_EINVAL;
+  if (p->v.n == 0 || !p->v.cache) return CELESTE_OK;
+  Launch L = make_launch(c, p);
+  CK(cudaMemsetAsync(p->v.active, 1, p->v.n, c->stream));
+  int rc = run_setup(c, p, 0, p->v.n_own_pairs, false);
+  if (rc) return rc;
+  ++c->launches;
+  return to_status(timed(c, CELESTE_K_RENDER, p->visits, L.stream,
+                         [&] { return launch_render_cache(L, p->v, nullptr); }));
 }
 
 int celeste_tr_subproblem(celeste_ctx* c, int32_t n, const double* g, const double* H,
@@ -651,226 +627,5 @@ int celeste_color_sources(int32_t n, const int32_t* nbr_ptr, const int32_t* nbr_
   return n_colors;
 }
 
-
-// ---- region fit -----------------------------------------------------------
-
-int celeste_fit_destroy(celeste_fit* F) {
-  if (!F) return CELESTE_EINVAL;
-  if (F->exec) cudaGraphExecDestroy(F->exec);
-  if (F->graph) cudaGraphDestroy(F->graph);
-  if (F->capture) cudaStreamDestroy(F->capture);
-  if (F->h_out) cudaFreeHost(F->h_out);
-  for (celeste_plan* p : F->plans) celeste_plan_destroy(p);
-  for (void* a : F->allocs) cudaFree(a);
-  delete F;
-  return CELESTE_OK;
-}
-
-int celeste_fit_create(celeste_ctx* c, const celeste_problem* pr, const int32_t* ids, int32_t n,
-                       const celeste_tuning* tuning, celeste_fit** out) {
-  if (!c || !pr || !out || n < 0 || (n > 0 && !ids) || !pr->h_nbr_ptr ||
-      (pr->n_nbr > 0 && !pr->h_nbr_idx))
-    return CELESTE_EINVAL;
-  *out = nullptr;
-  std::vector<int32_t> region(ids, ids + n);
-  std::sort(region.begin(), region.end());
-  for (int j = 0; j < n; ++j)
-    if (region[j] < 0 || region[j] >= pr->n_sources || (j > 0 && region[j] == region[j - 1]))
-      return CELESTE_EINVAL;
-  // greedy colouring of the region's overlap graph by ascending id
-  std::vector<int32_t> color(pr->n_sources, -1);
-  int n_colors = 0;
-  std::vector<char> used;
-  for (int s : region) {
-    used.assign(n_colors + 1, 0);
-    for (int k = pr->h_nbr_ptr[s]; k < pr->h_nbr_ptr[s + 1]; ++k) {
-      const int t = pr->h_nbr_idx[k];
-      if (t < 0 || t >= pr->n_sources) return CELESTE_EINVAL;
-      if (color[t] >= 0) used[color[t]] = 1;
-    }
-    int col = 0;
-    while (used[col]) ++col;
-    color[s] = col;
-    n_colors = std::max(n_colors, col + 1);
-  }
-  celeste_fit* F = new celeste_fit();
-  F->ctx = c;
-  F->region = region;
-  F->n_sources = pr->n_sources;
-  int rc = CELESTE_OK;
-  for (int col = 0; col < n_colors && rc == CELESTE_OK; ++col) {
-    std::vector<int32_t> cls;
-    for (int s : region)
-      if (color[s] == col) cls.push_back(s);
-    celeste_plan* p = nullptr;
-    rc = celeste_plan_create(c, pr, cls.data(), (int)cls.size(), tuning, &p);
-    if (rc == CELESTE_OK) F->plans.push_back(p);
-  }
-  auto alloc = [&](size_t bytes) -> void* {
-    void* ptr = nullptr;
-    if (rc != CELESTE_OK) return nullptr;
-    if (cudaMalloc(&ptr, bytes ? bytes : 1) != cudaSuccess) {
-      rc = CELESTE_ENOMEM;
-      return nullptr;
-    }
-    F->allocs.push_back(ptr);
-    return ptr;
-  };
-  const size_t S = (size_t)pr->n_sources;
-  FitView& f = F->f;
-  int32_t* d_region = static_cast<int32_t*>(alloc(n * sizeof(int32_t)));
-  f.delta = static_cast<double*>(alloc(S * sizeof(double)));
-  f.status = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
-  f.iters_pass = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
-  f.iters_total = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
-  f.accepted = static_cast<int32_t*>(alloc(S * sizeof(int32_t)));
-  f.done = static_cast<uint8_t*>(alloc(S));
-  f.gain = static_cast<double*>(alloc(S * sizeof(double)));
-  f.class_iter = static_cast<int32_t*>(alloc(n_colors * sizeof(int32_t)));
-  f.out = static_cast<double*>(alloc((1 + n_colors) * sizeof(double)));
-  f.region = d_region;
-  f.n_region = n;
-  f.n_classes = n_colors;
-  if (rc == CELESTE_OK &&
-      (cudaMallocHost(&F->h_out, (1 + n_colors) * sizeof(double)) != cudaSuccess ||
-       cudaMemcpy(d_region, region.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-       cudaMemset(f.iters_total, 0, S * sizeof(int32_t)) != cudaSuccess ||
-       cudaMemset(f.accepted, 0, S * sizeof(int32_t)) != cudaSuccess ||
-       cudaMemset(f.status, 0, S * sizeof(int32_t)) != cudaSuccess ||
-       cudaStreamCreateWithFlags(&F->capture, cudaStreamNonBlocking) != cudaSuccess))
-    rc = CELESTE_ECUDA;
-  if (rc != CELESTE_OK) {
-    celeste_fit_destroy(F);
-    return rc;
-  }
-  *out = F;
-  return CELESTE_OK;
-}
-
-int celeste_fit_classes(const celeste_fit* F) { return F ? F->f.n_classes : -1; }
-
-// Builds the graph of one pass (see fit.cu) for the given iteration budget.
-static int fit_build(celeste_fit* F, int max_iter) {
-  celeste_ctx* c = F->ctx;
-  if (F->exec) cudaGraphExecDestroy(F->exec);
-  if (F->graph) cudaGraphDestroy(F->graph);
-  F->exec = nullptr;
-  F->graph = nullptr;
-  F->f.max_iter = max_iter;
-  const FitView f = F->f;
-  cudaStream_t cs = F->capture;
-  CK(cudaGraphCreate(&F->graph, 0));
-  std::vector<cudaGraphNode_t> deps;
-  auto begin = [&]() {
-    return cudaStreamBeginCaptureToGraph(cs, F->graph, deps.empty() ? nullptr : deps.data(),
-                                         nullptr, deps.size(), cudaStreamCaptureModeRelaxed);
-  };
-  auto end = [&]() {
-    cudaStreamCaptureStatus st;
-    const cudaGraphNode_t* d = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd);
-    if (e == cudaSuccess) deps.assign(d, d + nd);
-    cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    return e != cudaSuccess ? e : e2;
-  };
-  CK(begin());
-  cudaError_t e = launch_fit_reset(cs, f);
-  cudaError_t e2 = end();
-  CK(e);
-  CK(e2);
-  for (int k = 0; k < f.n_classes; ++k) {
-    celeste_plan* p = F->plans[k];
-    Launch L = make_launch(c, p);
-    L.stream = cs;
-    // neighbour records and background, once per class and pass
-    CK(begin());
-    e = launch_mark_active(L, p->v, f.status);
-    if (e == cudaSuccess) e = launch_setup(L, p->v, c->d_model, 0, p->v.n_pairs, false);
-    if (e == cudaSuccess) e = launch_background(L, p->v);
-    e2 = end();
-    CK(e);
-    CK(e2);
-    cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, F->graph, 1, cudaGraphCondAssignDefault));
-    // (the parameter union has no default constructor: zeroed storage)
-    alignas(cudaGraphNodeParams) unsigned char np_bytes[sizeof(cudaGraphNodeParams)];
-    memset(np_bytes, 0, sizeof(np_bytes));
-    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_bytes);
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t loop;
-    CK(cudaGraphAddNode(&loop, F->graph, deps.empty() ? nullptr : deps.data(), nullptr,
-                        deps.size(), &np));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    e = enqueue_iteration(c, p, L, f.delta, f.status);
-    if (e == cudaSuccess) e = launch_fit_check(cs, p->v, f, p->rel_trial, k, h);
-    cudaGraph_t g = nullptr;
-    e2 = cudaStreamEndCapture(cs, &g);
-    CK(e);
-    CK(e2);
-    deps.assign(1, loop);
-  }
-  CK(begin());
-  e = launch_fit_pass_end(cs, f);
-  e2 = end();
-  CK(e);
-  CK(e2);
-  CK(cudaGraphInstantiate(&F->exec, F->graph, 0));
-  F->built_max_iter = max_iter;
-  return CELESTE_OK;
-}
-
-int celeste_fit_run(celeste_ctx* c, celeste_fit* F, int32_t max_passes, int32_t max_iter,
-                    double pass_tol, int32_t* passes_out, double* pass_gain) {
-  if (!c || !F || F->ctx != c || max_passes < 0 || max_passes > 1000 || max_iter < 0 ||
-      max_iter > 1000 || !(pass_tol >= 0.0))
-    return CELESTE_EINVAL;
-  if (max_passes == 0) max_passes = 5;
-  if (max_iter == 0) max_iter = 50;
-  if (passes_out) *passes_out = 0;
-  if (F->f.n_region == 0) return CELESTE_OK;
-  if (!F->exec || F->built_max_iter != max_iter) {
-    const int rc = fit_build(F, max_iter);
-    if (rc) return rc;
-  }
-  const FitView& f = F->f;
-  const size_t S = (size_t)F->n_sources;
-  CK(cudaMemsetAsync(f.iters_total, 0, S * sizeof(int32_t), c->stream));
-  CK(cudaMemsetAsync(f.accepted, 0, S * sizeof(int32_t), c->stream));
-  int pass = 0;
-  while (pass < max_passes) {
-    CK(cudaGraphLaunch(F->exec, c->stream));
-    CK(cudaMemcpyAsync(F->h_out, f.out, (1 + f.n_classes) * sizeof(double),
-                       cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    ++pass;
-    // launches of the pass: reset and summary, per class 3 + the loop trips
-    int64_t nl = 2;
-    for (int k = 0; k < f.n_classes; ++k)
-      nl += 3 + (int64_t)F->h_out[1 + k] * kIterationLaunches;
-    c->launches += nl;
-    if (pass_gain) pass_gain[pass - 1] = F->h_out[0];
-    if (!(F->h_out[0] > pass_tol * f.n_region)) break;
-  }
-  if (passes_out) *passes_out = pass;
-  return CELESTE_OK;
-}
-
-int celeste_fit_results(celeste_ctx* c, const celeste_fit* F, int32_t* status, int32_t* iters,
-                        int32_t* accepted, double* delta) {
-  if (!c || !F || F->ctx != c) return CELESTE_EINVAL;
-  const size_t S = (size_t)F->n_sources;
-  const FitView& f = F->f;
-  if (status) CK(cudaMemcpyAsync(status, f.status, S * 4, cudaMemcpyDeviceToDevice, c->stream));
-  if (iters) CK(cudaMemcpyAsync(iters, f.iters_total, S * 4, cudaMemcpyDeviceToDevice, c->stream));
-  if (accepted) CK(cudaMemcpyAsync(accepted, f.accepted, S * 4, cudaMemcpyDeviceToDevice, c->stream));
-  if (delta) CK(cudaMemcpyAsync(delta, f.delta, S * 8, cudaMemcpyDeviceToDevice, c->stream));
-  return CELESTE_OK;
-}
 
 }  // extern "C"

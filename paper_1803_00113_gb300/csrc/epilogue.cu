@@ -515,7 +515,8 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
   if (lane == 0) {
     if (elbo) elbo[j] = Lfull;
     if (elbo_rel) elbo_rel[j] = Lrel;
-    if (!isfinite(Lfull)) set_error(v.err, CELESTE_DERR_NONFINITE);
+    // a non-finite value at a trial point is a rejected step, not an error
+    if (!isfinite(Lfull) && !use_trial) set_error(v.err, CELESTE_DERR_NONFINITE);
   }
   if (kMode >= 1) {
     bool bad = false;

@@ -110,6 +110,9 @@ struct PlanView {
   double* hess;               // [n][27][27]
   uint8_t* active;            // [n] 1 if the slot takes part in the evaluation
   unsigned int* err;          // device error word
+  float2* cache;              // problem render cache (pool layout) or null
+  float2* trial_render;       // [n_bg] own moments at the trial point (with a cache)
+  const celeste_patch* patches;  // problem patches (pool offsets)
   int32_t n, n_pairs, n_own_pairs, n_items;
   int64_t n_bg;
 };
@@ -131,11 +134,20 @@ cudaError_t launch_setup(const Launch& L, const PlanView& v, const ModelDev* mod
 cudaError_t launch_background(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v);
-cudaError_t launch_pixels_value(const Launch& L, const PlanView& v);
+// keep_render: also store the own moments in v.trial_render (for a later
+// commit to the render cache of the sources whose step is accepted)
+cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render = false);
 cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, float* V_out,
                           const celeste_patch* patches);
 cudaError_t launch_background_out(const Launch& L, const PlanView& v, float* bgE, float* bgV,
                                   const celeste_patch* patches);
+// Own moments of the plan's pairs into v.cache: every slot, or (status
+// non-null) only slots whose source's status is CELESTE_ST_ACCEPTED, whose
+// records then hold the accepted trial point.
+cudaError_t launch_render_cache(const Launch& L, const PlanView& v, const int32_t* status);
+// Copies v.trial_render into the render cache for slots whose source's
+// status is CELESTE_ST_ACCEPTED.
+cudaError_t launch_commit_render(const Launch& L, const PlanView& v, const int32_t* status);
 // epilogue.cu
 cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* model,
                             double* elbo, double* elbo_rel, double* grad, double* hess);
@@ -153,10 +165,14 @@ cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const 
 cudaError_t launch_mark_active(const Launch& L, const PlanView& v, const int32_t* status);
 
 // fit.cu: the region fit's per-source state (device arrays indexed by source
-// id unless noted) and its bookkeeping kernels.
+// id unless noted) and its bookkeeping kernels.  The region is cut into
+// segments (independent requests), each with its own pass count and
+// stopping decision; a region fit has one segment.
 constexpr double kDelta0 = 1.0;   // initial trust radius of a subsolver call
 struct FitView {
-  const int32_t* region;   // [n_region] source ids of the region
+  const int32_t* region;   // [n_region] source ids, segment by segment
+  const int32_t* seg_ptr;  // [n_seg + 1] segment k = region[seg_ptr[k] .. seg_ptr[k+1])
+  const int32_t* seg_of;   // segment of each source id (region sources only)
   double* delta;
   int32_t* status;
   int32_t* iters_pass;     // Newton iterations in the current pass
@@ -165,8 +181,12 @@ struct FitView {
   uint8_t* done;           // retired for the rest of the pass
   double* gain;            // summed actual gain of accepted steps this pass
   int32_t* class_iter;     // [n_classes] loop trips of each class this pass
-  double* out;             // [1 + n_classes] pass summary
-  int32_t n_region, n_classes, max_iter;
+  uint8_t* seg_active;     // [n_seg] segment takes part in the next pass
+  int32_t* seg_passes;     // [n_seg] passes run
+  double* seg_gain;        // [n_seg] gain of the segment's last pass
+  int32_t* summary;        // [1 + n_classes]: active segments, class loop trips
+  int32_t n_region, n_seg, n_classes, max_iter, max_passes;
+  double pass_tol;         // a pass gaining <= pass_tol * (segment sources) ends it
 };
 cudaError_t launch_fit_reset(cudaStream_t stream, const FitView& f);
 cudaError_t launch_fit_check(cudaStream_t stream, const PlanView& v, const FitView& f,

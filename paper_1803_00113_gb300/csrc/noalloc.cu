@@ -241,6 +241,9 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
   v.partials = reinterpret_cast<float*>(S + o_part);
   v.active = S + o_active;
   v.err = reinterpret_cast<unsigned int*>(S + o_err);
+  v.cache = nullptr;            // backgrounds are always rendered here
+  v.trial_render = nullptr;
+  v.patches = pr->patches;
   v.n = n;
   v.n_pairs = np;
   v.n_own_pairs = n_own;

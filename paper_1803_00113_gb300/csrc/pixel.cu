@@ -430,7 +430,8 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
   }
 }
 
-__global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd) {
+__global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
+                                                    int keep_render) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
@@ -454,6 +455,7 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd) 
       float F0, F1, Es, Vs;
       profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
       own_moments(rec, F0, F1, Es, Vs);
+      if (keep_render) v.trial_render[pi.bg_base + q] = make_float2(Es, Vs);
       const float E = bg.x + Es, V = bg.y + Vs;
       const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
       rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
@@ -489,6 +491,39 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
       const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
       if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
       v.bg[pi.bg_base + q] = make_float2(s, 0.f);
+    }
+    if (v.cache) {
+      // gather the neighbours' cached moments (the values the render below
+      // would produce, added in the same order), 32 neighbour pairs at a
+      // time staged in the warp's shared memory
+      int4* srect = reinterpret_cast<int4*>(rec);
+      int64_t* soff = reinterpret_cast<int64_t*>(rec + 4 * 32);
+      const int nn = pi.nbr_end - pi.nbr_begin;
+      for (int c0 = 0; c0 < nn; c0 += 32) {
+        const int cnt = min(32, nn - c0);
+        __syncwarp();
+        if (lane < cnt) {
+          const PairInfo qn = v.pairs[v.pair_nbr[pi.nbr_begin + c0 + lane]];
+          srect[lane] = make_int4(qn.x0, qn.y0, qn.w, qn.h);
+          soff[lane] = v.patches[qn.patch].pool_offset;
+        }
+        __syncwarp();
+        for (int q = item.start + lane; q < end; q += 32) {
+          const int qy = q / pi.w;
+          const int gx = pi.x0 + (q - qy * pi.w), gy = pi.y0 + qy;
+          float2 b = v.bg[pi.bg_base + q];
+          for (int k = 0; k < cnt; ++k) {
+            const int4 r = srect[k];
+            const int lx = gx - r.x, ly = gy - r.y;
+            if (lx < 0 || ly < 0 || lx >= r.z || ly >= r.w) continue;
+            const float2 c = v.cache[soff[k] + ly * r.z + lx];
+            b.x += c.x;
+            b.y += c.y;
+          }
+          v.bg[pi.bg_base + q] = b;
+        }
+      }
+      continue;
     }
     for (int nb = pi.nbr_begin; nb < pi.nbr_end; ++nb) {
       const int np = v.pair_nbr[nb];
@@ -543,6 +578,48 @@ __global__ void __launch_bounds__(128) render_kernel(PlanView v, int ne, int nd,
   }
 }
 
+// Own E_s and V_s of the plan's pairs into the problem's render cache.
+__global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, int nd,
+                                                           const int32_t* __restrict__ status) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (status && status[pi.source] != CELESTE_ST_ACCEPTED) continue;
+    float2* out = v.cache + v.patches[pi.patch].pool_offset;
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      float F0, F1, Es, Vs;
+      profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
+      own_moments(rec, F0, F1, Es, Vs);
+      out[q] = make_float2(Es, Vs);
+    }
+  }
+}
+
+__global__ void commit_render_kernel(PlanView v, const int32_t* __restrict__ status) {
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    if (status[pi.source] != CELESTE_ST_ACCEPTED) continue;
+    float2* out = v.cache + v.patches[pi.patch].pool_offset;
+    for (int q = item.start + lane; q < item.start + item.count; q += 32)
+      out[q] = v.trial_render[pi.bg_base + q];
+  }
+}
+
 __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
                                   const celeste_patch* __restrict__ patches) {
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -590,10 +667,16 @@ cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pixels_value(const Launch& L, const PlanView& v) {
+cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render) {
   if (v.n_items == 0) return cudaSuccess;
   value_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
-      v, L.n_exp, L.n_dev);
+      v, L.n_exp, L.n_dev, keep_render && v.trial_render ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_render(const Launch& L, const PlanView& v, const int32_t* status) {
+  if (v.n_items == 0 || !v.cache || !v.trial_render) return cudaSuccess;
+  commit_render_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, 0, L.stream>>>(v, status);
   return cudaGetLastError();
 }
 
@@ -602,6 +685,13 @@ cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, floa
   if (v.n_items == 0) return cudaSuccess;
   render_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev, E_out, V_out, patches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_cache(const Launch& L, const PlanView& v, const int32_t* status) {
+  if (v.n_items == 0 || !v.cache) return cudaSuccess;
+  render_cache_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+      v, L.n_exp, L.n_dev, status);
   return cudaGetLastError();
 }
 
