@@ -2,9 +2,14 @@
 // the ball |p| <= Delta exactly, then accept or reject the trial point.
 //
 // GB300 issues a warp-wide FP64 instruction about every 64 cycles per SM
-// sub-partition, so the cost of this kernel is its count of FP64 warp
-// instructions, and a source gets four warps (one per sub-partition) for
-// the part that parallelises:
+// sub-partition, so the cost of this kernel is its count of dependent FP64
+// warp instructions, and a source gets four warps (one per sub-partition).
+// The usual path is mixed: FP32 locates lambda_min and the multiplier (a
+// Householder reduction and multisections, cheap on the FP32 pipes), then
+// FP64 computes the answer on the full matrix with one to three LDL^T
+// factorisations (safeguarded Newton on the secular equation).  Close to the
+// pole, and whenever FP64 contradicts the FP32 estimate, the all-FP64 path
+// below takes over:
 //   * B = -H is reduced to tridiagonal form T = Q^T B Q by Householder
 //     reflections; rows are spread over the lanes and columns over the four
 //     warps;
@@ -35,8 +40,27 @@ constexpr double kDeltaMax = 100.0;
 constexpr double kFtol = 1e-9;
 constexpr double kDeltaMin = 1e-8;
 
+constexpr int kTri = N * (N + 1) / 2;                        // 378 lower entries
+constexpr int kOwn = (kTri + kTrThreads - 1) / kTrThreads;   // 3 per thread
+
 struct TrSmem {
   double B[N * N];
+  // mixed-precision path
+  double W[N * N];                 // factorisation work copy of B + l I
+  double L[N * N];                 // unit lower factor of B + l I (strict lower part)
+  double Dinv[32];                 // 1 / D
+  double col[2][32];               // published pivot column, double-buffered
+  double p[32];
+  double lam, lo, hi;              // multiplier and its bracket (unscaled)
+  double lmin_lo;                  // lower bound of lambda_min (unscaled, FP32 accuracy)
+  double lam_b;                    // boundary start when an interior try fails (0: none)
+  int positive;                    // FP32 finds B positive definite
+  int tried0;                      // l = 0 has been evaluated
+  float Bf[N * N];
+  float betaf[32], dfr[32], efr[32], gfr[32];
+  float cps[N * 32], gps[N * 32];  // per-lane scratch of the FP32 secular solves ([i][lane])
+  short2 tri[kTri];                // lower entry e -> (row, column)
+  int mode;                        // 0 interior candidate, 1 boundary, 2 full FP64 path
   double beta[32];
   double gh[32];
   double d[32];
@@ -73,6 +97,19 @@ __device__ __forceinline__ int sturm32(const float (&d)[N], const float (&e2)[N]
   return cnt;
 }
 
+// The same count reading d and e2 from shared memory (broadcast loads).
+__device__ __forceinline__ int sturm32s(const float* d, const float* e2, float sigma) {
+  int cnt = 0;
+  float q = d[0] - sigma;
+  cnt += q < 0.f;
+  for (int i = 1; i < N; ++i) {
+    const float qp = q == 0.f ? 1e-30f : q;
+    q = (d[i] - sigma) - __fdividef(e2[i - 1], qp);
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
 // Sturm count of T - sigma I in FP64 without divisions: sign changes of the
 // characteristic-polynomial sequence p_0 = 1, p_1 = d_0 - sigma,
 // p_{i+1} = (d_i - sigma) p_i - e_{i-1}^2 p_{i-1} (scaled T keeps |p_i| <= 3^27).
@@ -96,13 +133,13 @@ __device__ __forceinline__ int sturm64(const double (&d)[N], const double (&e2)[
 __device__ __noinline__ float norm2_32(const float* d, const float* e, const float* g, float lam) {
   float cp[N], gp[N];
   float m = d[0] + lam;
-  float r = __frcp_rn(m);
+  float r = __fdividef(1.f, m);
   cp[0] = e[0] * r;
   gp[0] = g[0] * r;
 #pragma unroll
   for (int i = 1; i < N; ++i) {
     m = (d[i] + lam) - e[i - 1] * cp[i - 1];
-    r = __frcp_rn(m);
+    r = __fdividef(1.f, m);
     cp[i] = i < N - 1 ? e[i] * r : 0.f;
     gp[i] = (g[i] - e[i - 1] * gp[i - 1]) * r;
   }
@@ -113,6 +150,31 @@ __device__ __noinline__ float norm2_32(const float* d, const float* e, const flo
     s += y * y;
   }
   return s;
+}
+
+// |y|^2 for (T + lam I) y = g in FP32 with the per-lane elimination
+// factors in shared memory (cps, gps: [i][lane] layout, lane's column).
+__device__ float norm2_32s(const float* d, const float* e, const float* g, float lam, float* cps,
+                           float* gps) {
+  float m = d[0] + lam;
+  float r = __fdividef(1.f, m);
+  float c = e[0] * r, gp = g[0] * r;
+  cps[0] = c;
+  gps[0] = gp;
+  for (int i = 1; i < N; ++i) {
+    m = (d[i] + lam) - e[i - 1] * c;
+    r = __fdividef(1.f, m);
+    c = i < N - 1 ? e[i] * r : 0.f;
+    gp = (g[i] - e[i - 1] * gp) * r;
+    cps[i * 32] = c;
+    gps[i * 32] = gp;
+  }
+  float y = gp, sum = y * y;
+  for (int i = N - 2; i >= 0; --i) {
+    y = gps[i * 32] - cps[i * 32] * y;
+    sum += y * y;
+  }
+  return sum;
 }
 
 // LDL^T of T + lam I (positive definite; scaled T) and y = (T + lam I)^{-1} rhs.
@@ -168,11 +230,12 @@ __device__ void apply_q(TrSmem& S, double* x, bool transpose, int lane) {
   }
 }
 
-// Exact trust-region subproblem of one source; 128 threads (4 warps) enter,
-// warp 0 finishes: it returns true and holds p in S.y and the predicted
-// gain in S.red[0].  g (27) and H (27 x 27) are in global memory.
-__device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* __restrict__ H,
-                         double Delta) {
+// Exact trust-region subproblem of one source, all in FP64 (the path for
+// the hard and nearly hard cases); 128 threads (4 warps) enter, warp 0
+// finishes: it returns true and holds p in S.y and the predicted gain in
+// S.red[0].  g (27) and H (27 x 27) are in global memory.
+__device__ bool tr_solve_full(TrSmem& S, const double* __restrict__ g,
+                              const double* __restrict__ H, double Delta) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int e = tid; e < N * N; e += kTrThreads) {
     const int i = e / N, j = e % N;
@@ -437,6 +500,406 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   }
   __syncwarp();
   apply_q(S, S.y, false, lane);
+  return true;
+}
+
+// ---- mixed-precision path ---------------------------------------------------
+//
+// FP32 finds where the answer is, FP64 computes it: the FP32 Householder
+// reduction of B, Sturm multisection and secular-equation multisection give
+// lambda_min and the multiplier to ~1e-6 of the matrix scale; then the
+// safeguarded Newton iteration of Nocedal & Wright (Algorithm 4.3, one
+// LDL^T factorisation of the full B + l I per step, all in FP64) converges
+// from there in one to three steps.  Near the pole (the hard case or close
+// to it) and whenever FP64 contradicts FP32, the full FP64 path above runs.
+
+// 1/x in FP64 for any positive finite x (FP32 seed on a power-of-two
+// rescaled value, two Newton steps).
+__device__ __forceinline__ double rcp64_any(double x) {
+  int ex;
+  const double m = frexp(x, &ex);                  // x = m 2^ex, m in [0.5, 1)
+  double r = (double)__frcp_rn((float)m);
+  r = r * fma(-m, r, 2.0);
+  r = r * fma(-m, r, 2.0);
+  return ldexp(r, -ex);
+}
+
+__device__ __forceinline__ double B_diag0(const TrSmem& S, double lam) { return S.B[0] + lam; }
+
+// 1/d in FP64 from an FP32 seed and one Newton step (relative error
+// ~1e-14) when d is inside the FP32 range; 0 when d is not a positive
+// finite pivot.
+__device__ __forceinline__ double pivot_rcp(double d) {
+  if (!(d > 0.0 && d < 1e300)) return 0.0;
+  if (d > 1e-30 && d < 1e30) {
+    const double r = (double)__frcp_rn((float)d);
+    return fma(r, fma(-d, r, 1.0), r);
+  }
+  return rcp64_any(d);
+}
+
+// LDL^T of B + lam I in FP64 with all 128 threads, right-looking, one
+// barrier per column: the m(m+1)/2 entries of the trailing triangle are
+// spread evenly over the threads, each updated with the column's inverse
+// pivot applied on the fly; thread 0, which updates the next diagonal entry
+// first, takes its reciprocal right away.  The columns of L are scaled at
+// the end.  Returns false (the same on every thread) when a pivot is not
+// positive.  On success S.L holds the unit lower factor (strictly lower
+// part) and S.Dinv the inverse pivots.  S.W is the working copy.
+__device__ bool ldl_factor(TrSmem& S, double lam) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kTri; e += kTrThreads) {
+    const short2 t = S.tri[e];
+    S.W[t.x * N + t.y] = S.B[t.x * N + t.y] + (t.x == t.y ? lam : 0.0);
+  }
+  if (tid == 0) S.Dinv[0] = pivot_rcp(B_diag0(S, lam));
+  if (__syncthreads_or(tid == 0 && S.Dinv[0] == 0.0)) return false;
+  for (int j = 0; j < N - 1; ++j) {
+    const int m = N - 1 - j;
+    const int cnt = m * (m + 1) / 2;
+    const double dinv = S.Dinv[j];
+    int bad = 0;
+    for (int e = tid; e < cnt; e += kTrThreads) {
+      const short2 t = S.tri[e];                  // (row, col) in the trailing block
+      const int i = j + 1 + t.x, k = j + 1 + t.y;
+      const double w = fma(-(S.W[i * N + j] * dinv), S.W[k * N + j], S.W[i * N + k]);
+      S.W[i * N + k] = w;
+      if (e == 0) {                               // the next pivot
+        const double r = pivot_rcp(w);
+        S.Dinv[j + 1] = r;
+        bad = r == 0.0;
+      }
+    }
+    if (__syncthreads_or(bad)) return false;
+  }
+  for (int e = tid; e < kTri; e += kTrThreads) {
+    const short2 t = S.tri[e];
+    if (t.x > t.y) S.L[t.x * N + t.y] = S.W[t.x * N + t.y] * S.Dinv[t.y];
+  }
+  __syncthreads();
+  return true;
+}
+
+// Warp 0: p = (L D L^T)^{-1} rhs into out; returns |p|^2, and in *q2 (when
+// non-null) p^T (L D L^T)^{-1} p.  Rows live on lanes; each elimination step
+// broadcasts one solved entry.
+__device__ double ldl_solve_full(TrSmem& S, const double* rhs, double* out, int lane,
+                                 double* q2) {
+  double b = lane < N ? rhs[lane] : 0.0;
+  for (int k = 0; k < N - 1; ++k) {
+    const double wk = __shfl_sync(0xffffffffu, b, k);
+    if (lane > k && lane < N) b = fma(-S.L[lane * N + k], wk, b);
+  }
+  double z = lane < N ? b * S.Dinv[lane] : 0.0;
+  for (int k = N - 1; k > 0; --k) {
+    const double pk = __shfl_sync(0xffffffffu, z, k);
+    if (lane < k) z = fma(-S.L[k * N + lane], pk, z);
+  }
+  if (lane < N) out[lane] = z;
+  const double n2 = warp_sum_d(z * z);
+  if (q2) {
+    double u = z;
+    for (int k = 0; k < N - 1; ++k) {
+      const double uk = __shfl_sync(0xffffffffu, u, k);
+      if (lane > k && lane < N) u = fma(-S.L[lane * N + k], uk, u);
+    }
+    *q2 = warp_sum_d(lane < N ? u * u * S.Dinv[lane] : 0.0);
+    if (lane < N) S.z[lane] = u;        // u = L^{-1} p, for first_order()
+  }
+  __syncwarp();
+  return n2;
+}
+
+// Warp 0: p(l + dl) = p(l) - dl (B + l I)^{-1} p(l) to first order, with
+// (B + l I)^{-1} p = L^{-T} D^{-1} u and u = L^{-1} p kept by ldl_solve_full.
+__device__ void first_order(TrSmem& S, int lane, double dl) {
+  double z = lane < N ? S.z[lane] * S.Dinv[lane] : 0.0;
+  for (int k = N - 1; k > 0; --k) {
+    const double qk = __shfl_sync(0xffffffffu, z, k);
+    if (lane < k) z = fma(-S.L[k * N + lane], qk, z);
+  }
+  if (lane < N) S.p[lane] = fma(-dl, z, S.p[lane]);
+  __syncwarp();
+}
+
+// Householder reduction of B (FP32, in S.Bf) to tridiagonal form by warp 0
+// with rows on lanes and no block barrier; the reflections are applied to g
+// as they are made.  d, e into S.dfr, S.efr; Q^T g into S.gfr.
+__device__ void householder32(TrSmem& S) {
+  const int lane = threadIdx.x & 31;
+  float* Bf = S.Bf;
+  float* vs = S.ef;            // reflector, broadcast through shared memory
+  float* ws = S.e2f;           // w = p - K v
+  float gi = lane < N ? S.gfr[lane] : 0.f;
+  for (int k = 0; k < N - 2; ++k) {
+    const bool row = lane > k && lane < N;
+    const float xv = row ? Bf[lane * N + k] : 0.f;
+    float nrm2 = xv * xv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+    const float x0 = __shfl_sync(0xffffffffu, xv, k + 1);
+    if (lane == 0) S.dfr[k] = Bf[k * N + k];
+    if (!(nrm2 - x0 * x0 > 1e-30f * fmaxf(nrm2, 1e-30f))) {
+      if (lane == 0) S.efr[k] = x0;
+      continue;
+    }
+    const float alpha = -copysignf(sqrtf(nrm2), x0);
+    const float bt = __fdividef(1.f, fmaf(-x0, alpha, nrm2));
+    const float v = xv - (lane == k + 1 ? alpha : 0.f);
+    if (lane == 0) S.efr[k] = alpha;
+    vs[lane] = v;
+    __syncwarp();
+    // p = bt A v over the trailing block, four partial sums
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    if (row) {
+      const float* r = Bf + lane * N;
+      int c = k + 1;
+      for (; c + 3 < N; c += 4) {
+        p0 = fmaf(r[c], vs[c], p0);
+        p1 = fmaf(r[c + 1], vs[c + 1], p1);
+        p2 = fmaf(r[c + 2], vs[c + 2], p2);
+        p3 = fmaf(r[c + 3], vs[c + 3], p3);
+      }
+      for (; c < N; ++c) p0 = fmaf(r[c], vs[c], p0);
+    }
+    const float p = row ? bt * ((p0 + p1) + (p2 + p3)) : 0.f;
+    float K = v * p;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) K += __shfl_xor_sync(0xffffffffu, K, o);
+    const float w = fmaf(-0.5f * bt * K, v, p);
+    ws[lane] = w;
+    __syncwarp();
+    if (row) {
+      float* r = Bf + lane * N;
+      for (int c = k + 1; c < N; ++c) r[c] = fmaf(-v, ws[c], fmaf(-w, vs[c], r[c]));
+    }
+    // g -= bt v (v.g)
+    float vg = v * gi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vg += __shfl_xor_sync(0xffffffffu, vg, o);
+    gi = fmaf(-bt * vg, v, gi);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    S.dfr[N - 2] = Bf[(N - 2) * N + N - 2];
+    S.dfr[N - 1] = Bf[(N - 1) * N + N - 1];
+    S.efr[N - 2] = Bf[(N - 1) * N + N - 2];
+    S.efr[N - 1] = 0.f;
+  }
+  if (lane < N) S.gfr[lane] = gi;
+  __syncwarp();
+}
+
+// Warp 0: from the FP32 tridiagonal form, lambda_min and the multiplier to
+// FP32 accuracy; sets S.mode, S.lam, S.lo, S.hi (unscaled).
+__device__ void locate32(TrSmem& S, double Delta) {
+  const int lane = threadIdx.x & 31;
+  float rowf = 0.f, g2f = 0.f;
+  if (lane < N) {
+    rowf = fabsf(S.dfr[lane]) + fabsf(S.efr[lane]) + (lane ? fabsf(S.efr[lane - 1]) : 0.f);
+    g2f = S.gfr[lane] * S.gfr[lane];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rowf = fmaxf(rowf, __shfl_xor_sync(0xffffffffu, rowf, o));
+    g2f += __shfl_xor_sync(0xffffffffu, g2f, o);
+  }
+  const float scale = fmaxf(rowf, 1e-30f);
+  const float inv = 1.f / scale;
+  if (lane < N) {
+    S.df[lane] = S.dfr[lane] * inv;
+    S.ef[lane] = S.efr[lane] * inv;
+    S.e2f[lane] = S.ef[lane] * S.ef[lane];
+    S.gf[lane] = S.gfr[lane] * inv;
+  }
+  __syncwarp();
+  const float gnorm_s = sqrtf(g2f) * inv;
+  const float D2 = (float)(Delta * Delta);
+  float fa, fb;
+  {
+    fa = -1.f - 1e-6f;
+    fb = 1.f + 1e-6f;
+    for (int round = 0; round < 5; ++round) {
+      const float sig = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
+      const bool hit = lane < 31 && sturm32s(S.df, S.e2f, sig) >= 1;
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      const int t = mask ? __ffs(mask) - 1 : 31;
+      const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
+      const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
+      fa = na;
+      fb = nb;
+    }
+  }
+  // lambda_min (scaled) lies in [fa, fb] up to FP32 rounding of the counts
+  const float lmin = fa;
+  // mode 0: try l = 0 first (interior Newton step); mode 1: the boundary
+  // root from the bracket [la, lb]; mode 2: the all-FP64 path
+  int mode = 1;
+  float la = 0.f, lb = 0.f;
+  bool bracket = false;
+  const float n0 = lmin > 0.f ? norm2_32s(S.df, S.ef, S.gf, 0.f, S.cps + lane, S.gps + lane)
+                              : 3.4e38f;
+  if (!(g2f > 0.f)) {
+    mode = 2;
+  } else if (lmin > 1e-4f && n0 <= D2 * 0.999f) {
+    mode = 0;                       // clearly interior
+  } else {
+    // FP32 cannot tell an interior step of an ill-conditioned B from a
+    // boundary one: try l = 0 in FP64 when it may be interior, with the
+    // boundary bracket as the alternative
+    if (lmin > 0.f && n0 <= D2 * 1.01f) mode = 0;
+    bracket = true;
+    const float lo = fmaxf(0.f, -lmin);
+    la = lo;
+    lb = lo + gnorm_s / (float)Delta * 1.01f + 1e-6f;
+    for (int round = 0; round < 6; ++round) {
+      const float l = la + (lb - la) * (float)(lane + 1) * (1.f / 32.f);
+      const bool inside = lane < 31 && norm2_32s(S.df, S.ef, S.gf, l, S.cps + lane, S.gps + lane) <= D2;
+      const unsigned mask = __ballot_sync(0xffffffffu, inside);
+      const int t = mask ? __ffs(mask) - 1 : 31;
+      const float na = t == 0 ? la : la + (lb - la) * (float)t * (1.f / 32.f);
+      const float nb = t == 31 ? lb : la + (lb - la) * (float)(t + 1) * (1.f / 32.f);
+      la = na;
+      lb = nb;
+    }
+    // near the pole (nearly hard case) the FP32 bracket is still a good
+    // start; the FP64 iteration below resolves it, and a true hard case
+    // (no root above the pole) ends in the all-FP64 path
+  }
+  if (lane == 0) {
+    S.mode = mode;
+    const double sc = (double)scale;
+    S.lmin_lo = (double)scale * (double)fa;
+    S.positive = lmin > 0.f ? 1 : 0;
+    // the FP32 root estimate starts the FP64 iteration (0: no estimate)
+    S.lam = bracket ? sc * 0.5 * ((double)la + (double)lb) : 0.0;
+    S.lam_b = S.lam;
+    S.tried0 = 0;
+    if (mode == 0) S.lam = 0.0;
+    S.lo = -1.0;                      // FP64 bounds: none yet
+    S.hi = -1.0;
+  }
+  __syncwarp();
+}
+
+// Exact trust-region subproblem of one source; 128 threads (4 warps) enter,
+// warp 0 finishes: it returns true and holds p in S.y and the predicted
+// gain in S.red[0].  g (27) and H (27 x 27) are in global memory.
+__device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* __restrict__ H,
+                         double Delta) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int e = tid; e < N * N; e += kTrThreads) {
+    const int i = e / N, j = e % N;
+    const double b = -0.5 * (H[i * N + j] + H[j * N + i]);
+    S.B[e] = b;
+    S.Bf[e] = (float)b;
+  }
+  for (int e = tid; e < kTri; e += kTrThreads) {
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    S.tri[e] = make_short2((short)i, (short)(e - i * (i + 1) / 2));
+  }
+  if (tid < N) {
+    S.gh[tid] = g[tid];
+    S.gfr[tid] = (float)g[tid];
+  }
+  __syncthreads();
+  if (wid == 0) {
+    householder32(S);
+    locate32(S, Delta);
+  }
+  __syncthreads();
+  const double D2 = Delta * Delta;
+  bool done = false;
+  if (S.mode != 2) {
+    // safeguarded Newton on 1/|p(l)| - 1/Delta from the FP32 estimate;
+    // S.mode / S.lam / S.lo / S.hi are read after a barrier and written by
+    // warp 0 lane 0 only between barriers
+    for (int it = 0; it < 8 && !done; ++it) {
+      const double lam = S.lam;
+      const bool ok = ldl_factor(S, lam);
+      if (wid == 0) {
+        // Bounds known in FP64 (the FP32 estimates only pick the start):
+        // lo, a multiplier too small (indefinite, or |p| > Delta), < 0 for
+        // none; hi, one large enough (|p| <= Delta), < 0 for none
+        double lo = S.lo, hi = S.hi, next = lam;
+        int mode = S.mode, tried0 = S.tried0 | (lam == 0.0);
+        bool fin = false;
+        if (!ok) {
+          lo = fmax(lo, lam);
+          if (mode == 0 && S.lam_b > lo && (hi < 0.0 || S.lam_b < hi)) {
+            next = S.lam_b;
+          } else {
+            next = hi >= 0.0 ? 0.5 * (lo + hi) : 2.0 * lam + 1e-12 * (1.0 + fabs(S.lmin_lo));
+          }
+          mode = 1;
+        } else {
+          double q2;
+          const double n2 = ldl_solve_full(S, S.gh, S.p, lane, &q2);
+          const double np = sqrt(n2);
+          if (lam == 0.0 && n2 <= D2) {
+            fin = true;                 // interior Newton step
+          } else if (fabs(np - Delta) <= 1e-12 * Delta) {
+            fin = true;
+          } else {
+            if (n2 > D2) lo = fmax(lo, lam);
+            else hi = hi < 0.0 ? lam : fmin(hi, lam);
+            if (mode == 0 && S.lam_b > lo && (hi < 0.0 || S.lam_b < hi)) {
+              next = S.lam_b;           // l = 0 was not interior: start on the boundary
+            } else {
+              const double dl = (np - Delta) / Delta * n2 / q2;
+              double ln = lam + dl;
+              // a correction far below the distance to the pole: the
+              // first-order step leaves a relative error of about
+              // (dl / gap)^2 <= 1e-10 in p
+              const double gap = lam + S.lmin_lo;
+              const bool inside = ln > fmax(lo, 0.0) && (hi < 0.0 || ln < hi);
+              if (inside && gap > 0.0 && fabs(dl) <= 1e-5 * gap) {
+                first_order(S, lane, dl);
+                fin = true;
+              } else if (inside) {
+                next = ln;
+              } else if (n2 <= D2 && !tried0 && lo < 0.0) {
+                next = 0.0;             // the root may be at 0: an interior step
+              } else if (hi >= 0.0) {
+                next = 0.5 * (fmax(lo, 0.0) + hi);
+              } else {
+                next = 2.0 * lam + 1e-12 * (1.0 + fabs(S.lmin_lo));
+              }
+              if (next == lam) fin = true;
+            }
+          }
+          mode = 1;
+        }
+        if (lane == 0) {
+          S.lo = lo;
+          S.hi = hi;
+          S.lam = next;
+          S.tried0 = tried0;
+          S.mode = fin ? 3 : mode;
+        }
+      }
+      __syncthreads();
+      if (S.mode == 3) done = true;
+      if (S.mode == 2) break;
+    }
+  }
+  if (!done) {
+    __syncthreads();
+    return tr_solve_full(S, g, H, Delta);
+  }
+  if (wid != 0) return false;
+  // predicted gain g.p - p.B.p / 2 in FP64 on the full matrix, one row per lane
+  double term = 0.0;
+  if (lane < N) {
+    double bp = 0.0;
+    for (int k = 0; k < N; ++k) bp = fma(S.B[lane * N + k], S.p[k], bp);
+    term = S.p[lane] * fma(-0.5, bp, S.gh[lane]);
+  }
+  term = warp_sum_d(term);
+  if (lane < N) S.y[lane] = S.p[lane];
+  if (lane == 0) S.red[0] = term;
+  __syncwarp();
   return true;
 }
 
