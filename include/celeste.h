@@ -158,7 +158,8 @@ typedef struct celeste_problem {
 typedef struct celeste_tuning {
   int32_t pixels_per_item;    /* default pixels per item, 32..65536 */
   int32_t warps_per_block;    /* reserved (the pixel kernels use 4) */
-  int32_t blocks_per_sm;      /* persistent grid = SMs * blocks_per_sm (0 = 3) */
+  int32_t blocks_per_sm;      /* persistent grid = SMs * blocks_per_sm (0 = as many
+                                 as fit on an SM, per kernel) */
   int32_t reserved;
   int32_t ppi_bucket[4];      /* per patch-area bucket, 0 = pixels_per_item */
 } celeste_tuning;

@@ -18,7 +18,7 @@ Launch celeste::make_launch(const celeste_ctx* c, const celeste_plan* p) {
   L.stream = c->stream;
   L.sm_count = c->sm_count;
   L.warps_per_block = p && p->tuning.warps_per_block > 0 ? p->tuning.warps_per_block : 4;
-  L.blocks_per_sm = p && p->tuning.blocks_per_sm > 0 ? p->tuning.blocks_per_sm : 3;
+  L.blocks_per_sm = p && p->tuning.blocks_per_sm > 0 ? p->tuning.blocks_per_sm : 0;
   L.pixels_per_item = p && p->tuning.pixels_per_item > 0 ? p->tuning.pixels_per_item : 256;
   L.n_exp = c->n_exp;
   L.n_dev = c->n_dev;
@@ -206,6 +206,7 @@ int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* 
   c->n_exp = m->n_exp;
   c->n_dev = m->n_dev;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      init_pixel_occupancy() != cudaSuccess ||
       cudaMalloc(&c->d_model, sizeof(ModelDev)) != cudaSuccess ||
       cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
       cudaMemcpy(c->d_model, &md, sizeof(md), cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -131,6 +131,9 @@ struct Launch {
 cudaError_t launch_setup(const Launch& L, const PlanView& v, const ModelDev* model,
                          int first_pair, int n_pairs, bool use_trial);
 // pixel.cu
+// Measures the resident blocks per SM of the pixel kernels (once, before any
+// stream capture; launches made earlier use 3 blocks per SM).
+cudaError_t init_pixel_occupancy();
 cudaError_t launch_background(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v);

@@ -24,6 +24,17 @@ namespace celeste {
 
 constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 
+// One Gaussian component of a staged record: two 16-byte shared-memory
+// loads (the record and each 8-float component are 16-byte aligned).
+struct Comp {
+  float mx, my, p11, p12, p22, lw, tau;
+};
+__device__ __forceinline__ Comp load_comp(const float* __restrict__ c) {
+  const float4 a = *reinterpret_cast<const float4*>(c);
+  const float4 b = *reinterpret_cast<const float4*>(c + 4);
+  return Comp{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+}
+
 // Sums over the components of one galaxy profile (weights without rho):
 // S*: derivatives in mu; T2: tau-weighted second order (-> dG);
 // T3: tau-weighted third order (-> d mu dG); T4: tau^2 fourth order (-> dG dG).
@@ -36,12 +47,13 @@ struct GalSums {
 
 __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, float px, float py,
                                                GalSums& g) {
-  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22], tau = c[C_TAU];
-  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const Comp cc = load_comp(c);
+  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22, tau = cc.tau;
+  const float dx = px - cc.mx, dy = py - cc.my;
   const float y1 = fmaf(P11, dx, P12 * dy);
   const float y2 = fmaf(P12, dx, P22 * dy);
   const float Q = fmaf(dx, y1, dy * y2);
-  const float phi = exp2f(fmaf(-kHalfLog2e, Q, c[C_LW]));
+  const float phi = exp2f(fmaf(-kHalfLog2e, Q, cc.lw));
   const float h11 = fmaf(y1, y1, -P11);
   const float h12 = fmaf(y1, y2, -P12);
   const float h22 = fmaf(y2, y2, -P22);
@@ -71,12 +83,13 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, floa
 }
 
 __device__ __forceinline__ float gauss_value(const float* __restrict__ c, float px, float py) {
-  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
-  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const Comp cc = load_comp(c);
+  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
+  const float dx = px - cc.mx, dy = py - cc.my;
   const float y1 = fmaf(P11, dx, P12 * dy);
   const float y2 = fmaf(P12, dx, P22 * dy);
   const float Q = fmaf(dx, y1, dy * y2);
-  return exp2f(fmaf(-kHalfLog2e, Q, c[C_LW]));
+  return exp2f(fmaf(-kHalfLog2e, Q, cc.lw));
 }
 
 // Galaxy (rho-mixed) and star profile densities of one pair at a pixel.
@@ -115,11 +128,12 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
     const float* c = rec + kHdr + k * kCompF;
-    const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
-    const float dx = px - c[C_MX], dy = py - c[C_MY];
+    const Comp cc = load_comp(c);
+    const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
+    const float dx = px - cc.mx, dy = py - cc.my;
     const float y1 = fmaf(P11, dx, P12 * dy);
     const float y2 = fmaf(P12, dx, P22 * dy);
-    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
+    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
     F1 += phi;
     sx = fmaf(phi, y1, sx);
     sy = fmaf(phi, y2, sy);
@@ -132,8 +146,14 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
   const int per = ne + nd;
   for (int k = 0; k < kPsf; ++k) {
     const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
-    for (int j = 0; j < ne; ++j) gal_accumulate(base + j * kCompF, px, py, ge);
-    for (int j = 0; j < nd; ++j) gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
+    // the two profiles' sums are independent chains: interleave them
+    const int nb = ne < nd ? ne : nd;
+    for (int j = 0; j < nb; ++j) {
+      gal_accumulate(base + j * kCompF, px, py, ge);
+      gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
+    }
+    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kCompF, px, py, ge);
+    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
   }
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
@@ -272,12 +292,13 @@ struct GalSums1 {
 
 __device__ __forceinline__ void gal_accumulate1(const float* __restrict__ c, float px, float py,
                                                 GalSums1& g) {
-  const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
-  const float dx = px - c[C_MX], dy = py - c[C_MY];
+  const Comp cc = load_comp(c);
+  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
+  const float dx = px - cc.mx, dy = py - cc.my;
   const float y1 = fmaf(P11, dx, P12 * dy);
   const float y2 = fmaf(P12, dx, P22 * dy);
-  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
-  const float pt = phi * c[C_TAU];
+  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
+  const float pt = phi * cc.tau;
   g.s0 += phi;
   g.s1x = fmaf(phi, y1, g.s1x);
   g.s1y = fmaf(phi, y2, g.s1y);
@@ -295,11 +316,12 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
     const float* c = rec + kHdr + k * kCompF;
-    const float P11 = c[C_P11], P12 = c[C_P12], P22 = c[C_P22];
-    const float dx = px - c[C_MX], dy = py - c[C_MY];
+    const Comp cc = load_comp(c);
+    const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
+    const float dx = px - cc.mx, dy = py - cc.my;
     const float y1 = fmaf(P11, dx, P12 * dy);
     const float y2 = fmaf(P12, dx, P22 * dy);
-    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c[C_LW]));
+    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
     F1 += phi;
     sx = fmaf(phi, y1, sx);
     sy = fmaf(phi, y2, sy);
@@ -308,8 +330,13 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
   const int per = ne + nd;
   for (int k = 0; k < kPsf; ++k) {
     const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
-    for (int j = 0; j < ne; ++j) gal_accumulate1(base + j * kCompF, px, py, ge);
-    for (int j = 0; j < nd; ++j) gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
+    const int nb = ne < nd ? ne : nd;
+    for (int j = 0; j < nb; ++j) {
+      gal_accumulate1(base + j * kCompF, px, py, ge);
+      gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
+    }
+    for (int j = nb; j < ne; ++j) gal_accumulate1(base + j * kCompF, px, py, ge);
+    for (int j = nb; j < nd; ++j) gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
   }
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
@@ -636,40 +663,65 @@ __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
   }
 }
 
-static int grid_for(const Launch& L, int n_items, int wpb) {
-  int blocks = L.sm_count * (L.blocks_per_sm > 0 ? L.blocks_per_sm : 4);
-  const int needed = (n_items + wpb - 1) / wpb;
-  return blocks < needed ? blocks : (needed > 0 ? needed : 1);
-}
-
 static size_t smem_bytes(int wpb) { return (size_t)wpb * kRecF * sizeof(float); }
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
+// Resident blocks per SM of each persistent pixel kernel (0 until measured).
+enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccKinds };
+static int g_occ[kOccKinds] = {0, 0, 0, 0, 0};
+
+cudaError_t init_pixel_occupancy() {
+  const size_t sm = smem_bytes(kWpb);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccDerivs], derivs_kernel,
+                                                                kWpb * 32, sm);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccGrad], grad_kernel, kWpb * 32, sm);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccValue], value_kernel, kWpb * 32, sm);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccBackground], background_kernel,
+                                                      kWpb * 32, sm);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccRender], render_cache_kernel,
+                                                      kWpb * 32, sm);
+  return e;
+}
+
+// Persistent grid: SMs x (the tuning's blocks per SM, else the kernel's
+// occupancy), no more blocks than the work needs.
+static int grid_for(const Launch& L, int n_items, int wpb, int occ_kind = -1) {
+  int per_sm = L.blocks_per_sm;
+  if (per_sm <= 0) per_sm = occ_kind >= 0 && g_occ[occ_kind] > 0 ? g_occ[occ_kind] : 3;
+  const int blocks = L.sm_count * per_sm;
+  const int needed = (n_items + wpb - 1) / wpb;
+  return blocks < needed ? blocks : (needed > 0 ? needed : 1);
+}
+
 cudaError_t launch_background(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  background_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  background_kernel<<<grid_for(L, v.n_items, kWpb, kOccBackground), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  derivs_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  derivs_kernel<<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  grad_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render) {
   if (v.n_items == 0) return cudaSuccess;
-  value_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  value_kernel<<<grid_for(L, v.n_items, kWpb, kOccValue), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev, keep_render && v.trial_render ? 1 : 0);
   return cudaGetLastError();
 }
@@ -690,7 +742,7 @@ cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, floa
 
 cudaError_t launch_render_cache(const Launch& L, const PlanView& v, const int32_t* status) {
   if (v.n_items == 0 || !v.cache) return cudaSuccess;
-  render_cache_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  render_cache_kernel<<<grid_for(L, v.n_items, kWpb, kOccRender), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev, status);
   return cudaGetLastError();
 }
