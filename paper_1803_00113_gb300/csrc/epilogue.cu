@@ -370,12 +370,27 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
       vbase += warp_sum_d(b);
       continue;
     }
+    // Sum of the pair's tile sums, one accumulator per lane: compensated
+    // (Kahan) FP32 summation, whose error does not grow with the number of
+    // tiles, instead of a dependent chain of FP64 adds (a 101 x 101 patch has
+    // 40 tiles per image, and an FP64 add costs ~64 cycles here).
     double w0 = 0.0, w1 = 0.0;
     if (kMode == 2 || lane < kGradAcc) {
+      float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
       for (int it = pi.item_begin; it < pi.item_end; ++it) {
-        w0 += (double)v.partials[(size_t)it * kAcc + lane];
-        if (kMode == 2) w1 += (double)v.partials[(size_t)it * kAcc + 32 + lane];
+        const float y0 = v.partials[(size_t)it * kAcc + lane] - c0;
+        const float t0 = s0 + y0;
+        c0 = (t0 - s0) - y0;
+        s0 = t0;
+        if (kMode == 2) {
+          const float y1 = v.partials[(size_t)it * kAcc + 32 + lane] - c1;
+          const float t1 = s1 + y1;
+          c1 = (t1 - s1) - y1;
+          s1 = t1;
+        }
       }
+      w0 = (double)s0 - (double)c0;
+      w1 = (double)s1 - (double)c1;
     }
     S.W[lane] = w0;
     S.W[lane + 32] = w1;
