@@ -293,6 +293,23 @@ int celeste_fit_run(celeste_ctx* ctx, celeste_fit* fit, int32_t max_passes, int3
 int celeste_fit_results(celeste_ctx* ctx, const celeste_fit* fit, int32_t* status,
                         int32_t* iters, int32_t* accepted, double* delta);
 
+/* The ELBO of the whole problem (Eq. elbo over every pixel of every image,
+ * Sec. 2.2.3 and 4.2.2): the sum over all image pixels of
+ * -E + x (log E - V / (2 E^2)), E = sky + the E_q of every source whose
+ * patch holds the pixel and V the sum of their V_q, minus the sum of KL_s
+ * over all sources; -log x! is excluded.  For monitoring fits.  A field
+ * object colours all sources (greedy, ascending id), holds one plan per
+ * colour class and per-image E and V buffers (8 bytes per image pixel).
+ * celeste_field_elbo writes out[0] = ELBO, out[1] = the pixel sum,
+ * out[2] = the KL sum (DEVICE array of 3 doubles) at the current theta;
+ * the result is deterministic.  The neighbour lists must name every pair
+ * of sources whose patches overlap (the colouring relies on it). */
+typedef struct celeste_field celeste_field;
+int celeste_field_create(celeste_ctx* ctx, const celeste_problem* problem,
+                         const celeste_tuning* tuning, celeste_field** out);
+int celeste_field_destroy(celeste_field* field);
+int celeste_field_elbo(celeste_ctx* ctx, celeste_field* field, double* out);
+
 /* ---- serving (region fits submitted by independent callers) ------------
  *
  * A server owns worker threads, each with its own context, stream and

@@ -122,6 +122,10 @@ def lib():
         "celeste_fit_classes": (ctypes.c_int, [P]),
         "celeste_fit_run": (ctypes.c_int, [P, P, I32, I32, D, ctypes.POINTER(I32), P]),
         "celeste_fit_results": (ctypes.c_int, [P, P, P, P, P, P]),
+        "celeste_field_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem),
+                                                ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
+        "celeste_field_destroy": (ctypes.c_int, [P]),
+        "celeste_field_elbo": (ctypes.c_int, [P, P, P]),
         "celeste_server_create": (ctypes.c_int, [ctypes.POINTER(_Model), ctypes.c_int,
                                                  ctypes.POINTER(_ServerConfig), ctypes.POINTER(P)]),
         "celeste_server_destroy": (ctypes.c_int, [P]),
@@ -153,6 +157,7 @@ def exported_symbols():
             "celeste_render_cache",
             "celeste_color_sources", "celeste_fit_create", "celeste_fit_destroy",
             "celeste_fit_classes", "celeste_fit_run", "celeste_fit_results",
+            "celeste_field_create", "celeste_field_destroy", "celeste_field_elbo",
             "celeste_server_create", "celeste_server_destroy", "celeste_server_pause",
             "celeste_submit", "celeste_poll", "celeste_server_stats",
             "celeste_elbo_grad_hess_noalloc"]
@@ -530,6 +535,37 @@ class Fit:
     def close(self):
         if getattr(self, "handle", None):
             lib().celeste_fit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FieldElbo:
+    """The ELBO of the whole problem (celeste_field_*)."""
+
+    def __init__(self, ctx: Context, dprob: DeviceProblem, pixels_per_item: int = 0):
+        self.ctx = ctx
+        self.dprob = dprob
+        t = _Tuning(pixels_per_item, 0, 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().celeste_field_create(ctx.handle, ctypes.byref(dprob.struct), ctypes.byref(t),
+                                          ctypes.byref(h)), "celeste_field_create")
+        self.handle = h
+        self.out = torch.zeros(3, dtype=torch.float64, device=ctx.device)
+
+    def __call__(self):
+        """(ELBO, pixel sum, KL sum) at the current theta, as a device tensor."""
+        _check(lib().celeste_field_elbo(self.ctx.handle, self.handle, _ptr(self.out)),
+               "celeste_field_elbo")
+        return self.out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_field_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

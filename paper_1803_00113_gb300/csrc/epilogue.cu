@@ -584,4 +584,30 @@ cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const Mode
   return cudaGetLastError();
 }
 
+// KL_s of every slot's source at theta, into kl_out[source id] (for the
+// full-field ELBO, Eq. elbo: the pixel sum minus the sum of the KL_s).
+__global__ void kl_kernel(PlanView v, const ModelDev* __restrict__ model, double* kl_out) {
+  extern __shared__ double smd[];
+  EpiSmem& S = *reinterpret_cast<EpiSmem*>(smd);
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int src = v.src_ids[j];
+  if (lane < kTheta) S.th[lane] = (real)v.theta[(size_t)src * kTheta + lane];
+  __syncwarp();
+  kl_terms<0>(S.th, model, S, lane);
+  __syncwarp();
+  if (lane == 0) kl_out[src] = (double)S.kls[0];
+}
+
+cudaError_t launch_kl(const Launch& L, const PlanView& v, const ModelDev* model, double* kl_out) {
+  if (v.n == 0) return cudaSuccess;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(kl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EpiSmem));
+    done = true;
+  }
+  kl_kernel<<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, kl_out);
+  return cudaGetLastError();
+}
+
 }  // namespace celeste

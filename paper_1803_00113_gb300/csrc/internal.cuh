@@ -148,6 +148,18 @@ cudaError_t launch_background_out(const Launch& L, const PlanView& v, float* bgE
 // non-null) only slots whose source's status is CELESTE_ST_ACCEPTED, whose
 // records then hold the accepted trial point.
 cudaError_t launch_render_cache(const Launch& L, const PlanView& v, const int32_t* status);
+// Full-field ELBO pieces: own moments added into per-image buffers (pixel
+// pool layout; the plan's sources must not share pixels), the pixel term
+// over every image pixel into per-block partials, and the final sums.
+cudaError_t launch_accumulate(const Launch& L, const PlanView& v, float* Eimg, float* Vimg);
+cudaError_t launch_field_terms(const Launch& L, const celeste_image* images, int n_images,
+                               int blocks_per_image, const float* pixels, const float* sky,
+                               const float* Eimg, const float* Vimg, unsigned int* err,
+                               double* parts);
+cudaError_t launch_field_sum(const Launch& L, const double* parts, int n_parts, const double* kl,
+                             int n_kl, double* out);
+// epilogue.cu: KL_s of each slot's source at theta into kl_out[source id].
+cudaError_t launch_kl(const Launch& L, const PlanView& v, const ModelDev* model, double* kl_out);
 // Copies v.trial_render into the render cache for slots whose source's
 // status is CELESTE_ST_ACCEPTED.
 cudaError_t launch_commit_render(const Launch& L, const PlanView& v, const int32_t* status);

@@ -647,6 +647,101 @@ __global__ void commit_render_kernel(PlanView v, const int32_t* __restrict__ sta
   }
 }
 
+// Adds the plan's own moments into per-image buffers in the pixel-pool
+// layout.  Plain read-modify-write: sources of one colour class never share
+// a pixel, and classes are launched one after another.
+__global__ void __launch_bounds__(128) accumulate_kernel(PlanView v, int ne, int nd, float* Eimg,
+                                                         float* Vimg) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+    const Item item = v.items[it];
+    const PairInfo pi = v.pairs[item.pair];
+    __syncwarp();
+    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    __syncwarp();
+    const int end = item.start + item.count;
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      float F0, F1, Es, Vs;
+      profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
+      own_moments(rec, F0, F1, Es, Vs);
+      const int64_t m = pi.pix_base + (int64_t)qy * pi.stride + qx;
+      Eimg[m] += Es;
+      Vimg[m] += Vs;
+    }
+  }
+}
+
+// Pixel term -E + x (log E - V / (2 E^2)) (Eq. eq:log_p_last, without
+// log x!) over every pixel of image blockIdx.y, with E = sky + Eimg and
+// V = Vimg; compensated FP32 sums per thread, FP64 across threads; one
+// partial per block in parts[blockIdx.y * gridDim.x + blockIdx.x].
+__global__ void __launch_bounds__(256) field_term_kernel(const celeste_image* __restrict__ images,
+                                                         const float* __restrict__ pixels,
+                                                         const float* __restrict__ sky,
+                                                         const float* __restrict__ Eimg,
+                                                         const float* __restrict__ Vimg,
+                                                         unsigned int* err, double* parts) {
+  const celeste_image& im = images[blockIdx.y];
+  const int64_t n = (int64_t)im.height * im.width;
+  float s = 0.f, c = 0.f;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(f / im.width), x = (int)(f - (int64_t)y * im.width);
+    const int64_t m = im.pix_offset + (int64_t)y * im.row_stride + x;
+    const float sk = sky_value(im, sky, (float)x, (float)y);
+    if (!(sk > 0.f)) set_error(err, CELESTE_DERR_SKY);
+    const float E = sk + Eimg[m], V = Vimg[m], cnt = pixels[m];
+    const float r = __frcp_rn(E);
+    const float t = fmaf(cnt, __logf(E) - 0.5f * V * r * r, -E);
+    const float yk = t - c;
+    const float tk = s + yk;
+    c = (tk - s) - yk;
+    s = tk;
+  }
+  double d = (double)s - (double)c;
+  d = warp_sum_d(d);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    parts[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+// out[0] = sum parts - sum kl; out[1] = sum parts; out[2] = sum kl (fixed
+// order, one block).
+__global__ void __launch_bounds__(256) field_sum_kernel(const double* parts, int n_parts,
+                                                        const double* kl, int n_kl, double* out) {
+  __shared__ double red[2][256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_parts; i += blockDim.x) a += parts[i];
+  for (int i = threadIdx.x; i < n_kl; i += blockDim.x) b += kl[i];
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[1] = red[0][0];
+    out[2] = red[1][0];
+    out[0] = red[0][0] - red[1][0];
+  }
+}
+
 __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
                                   const celeste_patch* __restrict__ patches) {
   const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -744,6 +839,29 @@ cudaError_t launch_render_cache(const Launch& L, const PlanView& v, const int32_
   if (v.n_items == 0 || !v.cache) return cudaSuccess;
   render_cache_kernel<<<grid_for(L, v.n_items, kWpb, kOccRender), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
       v, L.n_exp, L.n_dev, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const Launch& L, const PlanView& v, float* Eimg, float* Vimg) {
+  if (v.n_items == 0) return cudaSuccess;
+  accumulate_kernel<<<grid_for(L, v.n_items, kWpb, kOccRender), kWpb * 32, smem_bytes(kWpb),
+                      L.stream>>>(v, L.n_exp, L.n_dev, Eimg, Vimg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_terms(const Launch& L, const celeste_image* images, int n_images,
+                               int blocks_per_image, const float* pixels, const float* sky,
+                               const float* Eimg, const float* Vimg, unsigned int* err,
+                               double* parts) {
+  if (n_images == 0) return cudaSuccess;
+  field_term_kernel<<<dim3(blocks_per_image, n_images), 256, 0, L.stream>>>(images, pixels, sky,
+                                                                            Eimg, Vimg, err, parts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_sum(const Launch& L, const double* parts, int n_parts, const double* kl,
+                             int n_kl, double* out) {
+  field_sum_kernel<<<1, 256, 0, L.stream>>>(parts, n_parts, kl, n_kl, out);
   return cudaGetLastError();
 }
 
