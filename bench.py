@@ -203,6 +203,15 @@ def cpu_baseline(problem, seconds, order=None):
                       f"{problem.n_sources} sources ({visits} visits, {t_total:.1f} s)"}
 
 
+def derivs_source_hash(path):
+    """Hash of the derivative kernel's source: pixel.cu up to the next kernel
+    (its device helpers and derivs_kernel itself)."""
+    import hashlib
+    text = open(path, "rb").read()
+    cut = text.find(b"__global__ void __launch_bounds__(128) grad_kernel")
+    return hashlib.sha256(text[:cut if cut > 0 else len(text)]).hexdigest()[:16]
+
+
 def traffic_per_launch(visits_per_launch):
     """DRAM bytes per derivative-kernel launch from the committed ncu summary,
     scaled by visits, when the summary was taken on the current kernel source."""
@@ -212,8 +221,7 @@ def traffic_per_launch(visits_per_launch):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if d.get("pixel_cu_sha256_16") != h:
+    if d.get("derivs_source_sha256_16") != derivs_source_hash(src):
         return None
     return d["dram_bytes_per_visit"] * visits_per_launch
 
