@@ -51,12 +51,15 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["field", "batched", "serving"], default="field")
+    ap.add_argument("--workload", choices=["field", "batched", "serving", "first-order"],
+                    default="field")
     ap.add_argument("--rates", default="50,200,500,1000,2000",
                     help="serving: Poisson arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="serving: arrival window per rate")
     ap.add_argument("--pool", type=int, default=96, help="serving: distinct requests generated")
+    ap.add_argument("--fo-max-steps", type=int, default=3000,
+                    help="first-order comparison: step cap of the L-BFGS subsolver")
     ap.add_argument("--sources", type=int, default=0, help="override the source count")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cache", action="store_true",
@@ -668,10 +671,108 @@ def run_serving(args):
             "gpu_launches": int(st["launches"]), "clocks": clk}
 
 
+# ---------------------------------------------------------------------------
+# Newton trust region vs a first-order subsolver (the paper's claim)
+# ---------------------------------------------------------------------------
+
+def run_first_order(args):
+    """Both subsolvers on the same per-source problems: the largest colour
+    class of the field, neighbours frozen at their start values.  Newton
+    runs until every source stops; L-BFGS (m = 10, Armijo backtracking) runs
+    until every source is within 1e-6 (1 + |L|) of the Newton optimum, or
+    until it stops, or for at most --fo-max-steps steps."""
+    import torch
+    world, rank, local = dist_info()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1803_00113_gb300 import build_lib
+    build_lib.build()
+    from paper_1803_00113_gb300 import celeste as cel
+    problem, cfg = workload("field", args.sources, SEED + 1)
+    ctx = cel.Context(problem.model, device=local)
+    dp = cel.DeviceProblem(problem, dev)
+    cls = max(cel.color_classes(problem), key=len)
+    plan = cel.Plan(ctx, dp, cls)
+    srcs = torch.as_tensor(plan.sources, dtype=torch.long, device=dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return out, time.perf_counter() - t0
+
+    # Newton: iterations per source until it stops
+    step_ms = []
+
+    def newton():
+        delta, status = cel.newton_state(dp)
+        its = torch.zeros(plan.n, dtype=torch.int32, device=dev)
+        for k in range(50):
+            live = (status[srcs] != cel.ST_CONVERGED) & (status[srcs] != cel.ST_FAILED)
+            its += live.int()
+            if not bool(live.any()):
+                break
+            t0 = time.perf_counter()
+            cel.newton_step(plan, delta, status)
+            torch.cuda.synchronize(dev)
+            step_ms.append((time.perf_counter() - t0) * 1e3)
+        return its
+    newton()                                              # warm-up (kernels, torch ops)
+    step_ms.clear()
+    dp.set_theta(problem.theta)
+    n_its, t_newton = timed(newton)
+    best = cel.elbo(plan)[1].clone()
+    dp.set_theta(problem.theta)
+    lb = cel.Lbfgs(plan, m=10)
+    target = best - 1e-6 * (1 + best.abs())
+
+    def first_order():
+        status = torch.zeros(problem.n_sources, dtype=torch.int32, device=dev)
+        steps = 0
+        for steps in range(1, args.fo_max_steps + 1):
+            lb.step(status, target)
+            if steps % 50 == 0:
+                reached = lb.counts()[2]
+                done = (reached > 0) | (status[srcs] == cel.ST_CONVERGED)
+                if bool(done.all()):
+                    break
+        return steps
+    lb.step(torch.zeros(problem.n_sources, dtype=torch.int32, device=dev), target)   # warm-up
+    lb.counts()
+    dp.set_theta(problem.theta)
+    lb.reset()
+    steps, t_fo = timed(first_order)
+    iters, fevals, reached = [t.cpu().numpy() for t in lb.counts()]
+    n_its = n_its.cpu().numpy()
+    ok = reached > 0
+    q = lambda a, f: float(np.percentile(a, f)) if len(a) else None
+    return {"metric": "time to the Newton optimum, L-BFGS over Newton trust region",
+            "value": t_fo / t_newton, "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": t_newton * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pixels, f64 subsolvers",
+            "data": "synthetic (seeded field shaped like the paper's study set)",
+            "config": dict(cfg, workload="first-order comparison on the largest colour class "
+                                         f"of the field ({plan.n} sources)"),
+            "newton": {"seconds": t_newton, "step_ms": [round(x, 3) for x in step_ms],
+                       "iterations_p50": q(n_its, 50),
+                       "iterations_p90": q(n_its, 90), "iterations_max": int(n_its.max())},
+            "lbfgs": {"seconds": t_fo, "steps": int(steps), "reached_fraction": float(ok.mean()),
+                      "gradient_evals_to_target_p50": q(reached[ok], 50),
+                      "gradient_evals_to_target_p90": q(reached[ok], 90),
+                      "gradient_evals_to_target_max": int(reached[ok].max()) if ok.any() else None,
+                      "trial_evals_total_p50": q(fevals, 50), "history": 10},
+            "e2e": None, "gpu_launches": int(ctx.launches())}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         line = run_reference(args)
+    elif args.workload == "first-order":
+        line = run_first_order(args)
     elif args.workload == "serving":
         line = run_serving(args)
     else:

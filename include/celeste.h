@@ -293,6 +293,36 @@ int celeste_fit_run(celeste_ctx* ctx, celeste_fit* fit, int32_t max_passes, int3
 int celeste_fit_results(celeste_ctx* ctx, const celeste_fit* fit, int32_t* status,
                         int32_t* iters, int32_t* accepted, double* delta);
 
+/* A first-order subsolver, to compare with the Newton trust-region one
+ * (Sec. 4.3 reports tens of Newton iterations against thousands for
+ * first-order methods and at times for BFGS): limited-memory BFGS (history
+ * m <= 16) on every source of the plan with a backtracking Armijo line
+ * search (c1 = 1e-4, unit step halved), neighbours frozen.  One call of
+ * celeste_lbfgs_step evaluates the value and gradient (the gradient-only
+ * pixel pass) of the sources whose last step was accepted, makes their new
+ * direction, and evaluates the value at the trial point of every source
+ * still running.  status[n_sources] (device, by source id): ACCEPTED,
+ * REJECTED (backtracking), CONVERGED when the model gain of the full
+ * quasi-Newton step, g.d / 2, is at most 1e-12 (1 + |L_rel|) or the step
+ * shrank to nothing.  A trial whose
+ * expected gain is below the value's FP32 noise (1e-7 (1 + |L_rel|)) is
+ * accepted unless the value drops by more than that noise.  Sources already
+ * CONVERGED/FAILED/MAXITER are skipped; initialise to 0.  target (device
+ * [n], plan order, may be NULL): L_rel values whose first crossing is
+ * recorded.  celeste_lbfgs_counts copies, per slot (device [n]), the
+ * accepted steps, the trial evaluations and the accepted steps at which the
+ * target was first reached (-1 if not).  celeste_lbfgs_reset clears the
+ * history and counters (not theta). */
+typedef struct celeste_lbfgs celeste_lbfgs;
+int celeste_lbfgs_create(celeste_ctx* ctx, const celeste_plan* plan, int32_t m,
+                         celeste_lbfgs** out);
+int celeste_lbfgs_destroy(celeste_lbfgs* lbfgs);
+int celeste_lbfgs_reset(celeste_ctx* ctx, celeste_lbfgs* lbfgs);
+int celeste_lbfgs_step(celeste_ctx* ctx, celeste_lbfgs* lbfgs, int32_t* status,
+                       const double* target);
+int celeste_lbfgs_counts(celeste_ctx* ctx, const celeste_lbfgs* lbfgs, int32_t* iters,
+                         int32_t* fevals, int32_t* reached);
+
 /* The ELBO of the whole problem (Eq. elbo over every pixel of every image,
  * Sec. 2.2.3 and 4.2.2): the sum over all image pixels of
  * -E + x (log E - V / (2 E^2)), E = sky + the E_q of every source whose

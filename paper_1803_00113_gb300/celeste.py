@@ -122,6 +122,11 @@ def lib():
         "celeste_fit_classes": (ctypes.c_int, [P]),
         "celeste_fit_run": (ctypes.c_int, [P, P, I32, I32, D, ctypes.POINTER(I32), P]),
         "celeste_fit_results": (ctypes.c_int, [P, P, P, P, P, P]),
+        "celeste_lbfgs_create": (ctypes.c_int, [P, P, I32, ctypes.POINTER(P)]),
+        "celeste_lbfgs_destroy": (ctypes.c_int, [P]),
+        "celeste_lbfgs_reset": (ctypes.c_int, [P, P]),
+        "celeste_lbfgs_step": (ctypes.c_int, [P, P, P, P]),
+        "celeste_lbfgs_counts": (ctypes.c_int, [P, P, P, P, P]),
         "celeste_field_create": (ctypes.c_int, [P, ctypes.POINTER(_Problem),
                                                 ctypes.POINTER(_Tuning), ctypes.POINTER(P)]),
         "celeste_field_destroy": (ctypes.c_int, [P]),
@@ -157,6 +162,8 @@ def exported_symbols():
             "celeste_render_cache",
             "celeste_color_sources", "celeste_fit_create", "celeste_fit_destroy",
             "celeste_fit_classes", "celeste_fit_run", "celeste_fit_results",
+            "celeste_lbfgs_create", "celeste_lbfgs_destroy", "celeste_lbfgs_reset",
+            "celeste_lbfgs_step", "celeste_lbfgs_counts",
             "celeste_field_create", "celeste_field_destroy", "celeste_field_elbo",
             "celeste_server_create", "celeste_server_destroy", "celeste_server_pause",
             "celeste_submit", "celeste_poll", "celeste_server_stats",
@@ -535,6 +542,44 @@ class Fit:
     def close(self):
         if getattr(self, "handle", None):
             lib().celeste_fit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lbfgs:
+    """The first-order comparison subsolver (celeste_lbfgs_*) on a plan."""
+
+    def __init__(self, plan: Plan, m: int = 10):
+        self.plan = plan
+        self.ctx = plan.ctx
+        h = ctypes.c_void_p()
+        _check(lib().celeste_lbfgs_create(self.ctx.handle, plan.handle, int(m), ctypes.byref(h)),
+               "celeste_lbfgs_create")
+        self.handle = h
+
+    def reset(self):
+        _check(lib().celeste_lbfgs_reset(self.ctx.handle, self.handle), "celeste_lbfgs_reset")
+
+    def step(self, status: torch.Tensor, target: Optional[torch.Tensor] = None):
+        _check(lib().celeste_lbfgs_step(self.ctx.handle, self.handle, _ptr(status), _ptr(target)),
+               "celeste_lbfgs_step")
+
+    def counts(self):
+        """(accepted steps, trial evaluations, steps to the target) per plan slot."""
+        n = self.plan.n
+        out = [torch.zeros(max(n, 1), dtype=torch.int32, device=self.ctx.device) for _ in range(3)]
+        _check(lib().celeste_lbfgs_counts(self.ctx.handle, self.handle, *[_ptr(t) for t in out]),
+               "celeste_lbfgs_counts")
+        return [t[:n] for t in out]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().celeste_lbfgs_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
