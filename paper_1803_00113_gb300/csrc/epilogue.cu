@@ -46,6 +46,8 @@ __device__ __forceinline__ real softplus(real t) {
   return t > 0.f ? t + log1pf(expf(-t)) : log1pf(expf(t));
 }
 
+constexpr int kEpiThreads = 128;   // four warps per source
+
 struct EpiSmem {
   double W[kAcc];                  // one pair's sums
   real th[kNuPad];                 // theta of the source (FP32 copy)
@@ -62,25 +64,23 @@ struct EpiSmem {
   real klj[2 * kMaxColor];         // log w_j - K_j
   real kls[8];                     // scalar KL pieces
   float T[10 * 10];                // per-image affine map w <- nu (local)
+  double Wp[2 * kAcc];             // per-half tile sums of one pair
+  double red[2][kEpiThreads / 32]; // per-warp value sums
 };
 
-// Rows a of J with J[a][c] != 0, for column c.
-__device__ __forceinline__ int col_rows(int c, int* rows) {
-  if (c == 0) {
-    for (int a = 0; a < 20; ++a) rows[a] = a;
-    return 20;
-  }
-  if (c <= 20) {
-    // type of the flux parameter: 1,2 | 3,4 | 5..8 | 9..12 | 13..16 | 17..20
-    const int i = c <= 4 ? (c - 1) / 2 : ((c - 5) / 4) & 1;
-    for (int k = 0; k < 10; ++k) rows[k] = 2 * k + i;   // kE_i and kM_i of every band
-    return 10;
-  }
-  if (c <= 22) { rows[0] = c - 1; return 1; }
-  if (c <= 25) { rows[0] = 22; rows[1] = 23; rows[2] = 24; return 3; }
-  rows[0] = 25;
-  return 1;
+// Rows a of J with J[a][c] != 0 for column c: their number and the k-th one
+// (the flux coordinates of a type feed every band's kE and kM rows).
+__device__ __forceinline__ int nrows(int c) {
+  return c == 0 ? 20 : (c <= 20 ? 10 : (c <= 22 ? 1 : (c <= 25 ? 3 : 1)));
 }
+__device__ __forceinline__ int rowof(int c, int k) {
+  if (c == 0) return k;
+  if (c <= 20) return 2 * k + (c <= 4 ? (c - 1) / 2 : ((c - 5) / 4) & 1);
+  if (c <= 22) return c - 1;
+  if (c <= 25) return 22 + k;
+  return 25;
+}
+
 
 // d log kappa / d theta for flux-moment coordinate a (0..19): band b = a / 4,
 // kind e = a % 4 (0: kE0, 1: kE1, 2: kM0, 3: kM1).  Returns kappa.
@@ -333,98 +333,104 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
   __syncwarp();
 }
 
-// kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian.
+// kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian.  Four
+// warps per source: the tile sums, the per-image maps and the two dense
+// products (X = H_nu J, H_theta += J^T X) are spread over 128 threads; the
+// KL terms and the Jacobian rows run on warp 0.
 template <int kMode>
-__global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, double* elbo,
-                                double* elbo_rel, double* grad_out, double* hess_out,
-                                int use_trial) {
+__global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
+                                                               const ModelDev* __restrict__ model,
+                                                               double* elbo, double* elbo_rel,
+                                                               double* grad_out, double* hess_out,
+                                                               int use_trial) {
   extern __shared__ double smd[];
   EpiSmem& S = *reinterpret_cast<EpiSmem*>(smd);
   const int j = blockIdx.x;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (!v.active[j]) return;
   const int src = v.src_ids[j];
   const double* thd = use_trial ? v.theta_trial + (size_t)j * kTheta : v.theta + (size_t)src * kTheta;
-  if (lane < kTheta) S.th[lane] = (real)thd[lane];
+  if (tid < kTheta) S.th[tid] = (real)thd[tid];
   const real* th = S.th;
 
   double vrel = 0.0, vbase = 0.0;
   if (kMode >= 1) {
-    for (int e = lane; e < kNuPad; e += 32) S.gnu[e] = 0.f;
-    for (int e = lane; e < kNuPad; e += 32) S.gth[e] = 0.f;
+    for (int e = tid; e < kNuPad; e += kEpiThreads) S.gnu[e] = 0.f;
+    for (int e = tid; e < kNuPad; e += kEpiThreads) S.gth[e] = 0.f;
   }
   if (kMode == 2) {
-    for (int e = lane; e < kNu * kNu; e += 32) S.Hnu[e] = 0.f;
-    for (int e = lane; e < kTheta * kTheta; e += 32) S.Hth[e] = 0.f;
+    for (int e = tid; e < kNu * kNu; e += kEpiThreads) S.Hnu[e] = 0.f;
+    for (int e = tid; e < kTheta * kTheta; e += kEpiThreads) S.Hth[e] = 0.f;
   }
-  __syncwarp();
+  __syncthreads();
   for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
     const PairInfo pi = v.pairs[pp];
     if (kMode == 0) {
       double r = 0.0, b = 0.0;
-      for (int it = pi.item_begin + lane; it < pi.item_end; it += 32) {
+      for (int it = pi.item_begin + tid; it < pi.item_end; it += kEpiThreads) {
         r += (double)v.vpartials[2 * (size_t)it];
         b += (double)v.vpartials[2 * (size_t)it + 1];
       }
-      vrel += warp_sum_d(r);
-      vbase += warp_sum_d(b);
+      r = warp_sum_d(r);
+      b = warp_sum_d(b);
+      if (lane == 0) {
+        S.red[0][wid] = r;
+        S.red[1][wid] = b;
+      }
+      __syncthreads();
+      for (int w = 0; w < kEpiThreads / 32; ++w) {
+        vrel += S.red[0][w];
+        vbase += S.red[1][w];
+      }
+      __syncthreads();
       continue;
     }
-    // Sum of the pair's tile sums, one accumulator per lane: compensated
-    // (Kahan) FP32 summation, whose error does not grow with the number of
-    // tiles, instead of a dependent chain of FP64 adds (a 101 x 101 patch has
-    // 40 tiles per image, and an FP64 add costs ~64 cycles here).
-    double w0 = 0.0, w1 = 0.0;
-    if (kMode == 2 || lane < kGradAcc) {
-      float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
-      for (int it = pi.item_begin; it < pi.item_end; ++it) {
-        const float y0 = v.partials[(size_t)it * kAcc + lane] - c0;
-        const float t0 = s0 + y0;
-        c0 = (t0 - s0) - y0;
-        s0 = t0;
-        if (kMode == 2) {
-          const float y1 = v.partials[(size_t)it * kAcc + 32 + lane] - c1;
-          const float t1 = s1 + y1;
-          c1 = (t1 - s1) - y1;
-          s1 = t1;
+    // Sum of the pair's tile sums: accumulator tid % 64, tiles of one parity
+    // per half of the block, compensated (Kahan) FP32 summation whose error
+    // does not grow with the number of tiles; the halves meet in FP64.
+    {
+      const int a = tid & (kAcc - 1), half = tid >> 6;
+      float s0 = 0.f, c0 = 0.f;
+      if (kMode == 2 || a < kGradAcc) {
+        for (int it = pi.item_begin + half; it < pi.item_end; it += 2) {
+          const float y0 = v.partials[(size_t)it * kAcc + a] - c0;
+          const float t0 = s0 + y0;
+          c0 = (t0 - s0) - y0;
+          s0 = t0;
         }
       }
-      w0 = (double)s0 - (double)c0;
-      w1 = (double)s1 - (double)c1;
+      S.Wp[half * kAcc + a] = (double)s0 - (double)c0;
     }
-    S.W[lane] = w0;
-    S.W[lane + 32] = w1;
+    if (tid < 100) S.T[tid] = 0.f;
+    __syncthreads();
     const celeste_image& im = v.images[pi.image];
-    // local affine map, FP32: w_k = sum_a T[k][a] nu_a
-    for (int e = lane; e < 100; e += 32) S.T[e] = 0.f;
-    __syncwarp();
-    {
+    if (tid < kAcc) S.W[tid] = S.Wp[tid] + S.Wp[kAcc + tid];
+    if (tid == kAcc) {
+      // local affine map, FP32: w_k = sum_a T[k][a] nu_a
       const float cal = (float)im.calib;
       const float A0 = (float)im.wcs_A[0], A1 = (float)im.wcs_A[1];
       const float A2 = (float)im.wcs_A[2], A3 = (float)im.wcs_A[3];
-      if (lane == 0) {
-        S.T[0] = cal;
-        S.T[11] = cal;
-        S.T[22] = cal * cal;
-        S.T[33] = cal * cal;
-        S.T[44] = A0; S.T[45] = A1; S.T[54] = A2; S.T[55] = A3;
-        S.T[66] = A0 * A0; S.T[67] = 2.f * A0 * A1; S.T[68] = A1 * A1;
-        S.T[76] = A0 * A2; S.T[77] = A0 * A3 + A1 * A2; S.T[78] = A1 * A3;
-        S.T[86] = A2 * A2; S.T[87] = 2.f * A2 * A3; S.T[88] = A3 * A3;
-        S.T[99] = 1.f;
-      }
+      S.T[0] = cal;
+      S.T[11] = cal;
+      S.T[22] = cal * cal;
+      S.T[33] = cal * cal;
+      S.T[44] = A0; S.T[45] = A1; S.T[54] = A2; S.T[55] = A3;
+      S.T[66] = A0 * A0; S.T[67] = 2.f * A0 * A1; S.T[68] = A1 * A1;
+      S.T[76] = A0 * A2; S.T[77] = A0 * A3 + A1 * A2; S.T[78] = A1 * A3;
+      S.T[86] = A2 * A2; S.T[87] = 2.f * A2 * A3; S.T[88] = A3 * A3;
+      S.T[99] = 1.f;
     }
-    __syncwarp();
+    __syncthreads();
     const int b = im.band;
     auto nu_of = [b](int a) { return a < 4 ? 4 * b + a : 16 + a; };   // 4..9 -> 20..25
     auto lo = [](int a) { return a < 4 ? a : (a < 6 ? 4 : (a < 9 ? 6 : 9)); };
     auto hi = [](int a) { return a < 4 ? a + 1 : (a < 6 ? 6 : (a < 9 ? 9 : 10)); };
-    if (lane < 10) {
+    if (tid < 10) {
       float gl = 0.f;
-      for (int k = lo(lane); k < hi(lane); ++k) gl += S.T[k * 10 + lane] * (float)S.W[2 + k];
-      S.gnu[nu_of(lane)] += gl;
-    }
-    for (int e = lane; e < (kMode == 2 ? 55 : 0); e += 32) {
+      for (int k = lo(tid); k < hi(tid); ++k) gl += S.T[k * 10 + tid] * (float)S.W[2 + k];
+      S.gnu[nu_of(tid)] += gl;
+    } else if (kMode == 2 && tid >= 32 && tid < 32 + 55) {
+      const int e = tid - 32;
       int a = 0, rem = e;
       while (rem >= 10 - a) { rem -= 10 - a; ++a; }
       const int c = a + rem;
@@ -442,108 +448,120 @@ __global__ void epilogue_kernel(PlanView v, const ModelDev* __restrict__ model, 
     }
     vrel += S.W[0];
     vbase += S.W[1];
-    __syncwarp();
+    __syncthreads();
   }
 
-  kl_terms<kMode>(th, model, S, lane);
+  if (wid == 0) kl_terms<kMode>(th, model, S, lane);
+  __syncthreads();
   const double kl = (double)S.kls[0];
   if (kMode >= 1) {
-    // Jacobian rows: flux moments (lanes 0..19), u, Sigma_s, rho
-    for (int e = lane; e < kNu * kTheta; e += 32) S.J[e] = 0.f;
-    __syncwarp();
-    if (lane < 20) {
-      real* dl = S.DL + lane * kTheta;
-      real* d2l = S.D2L + lane * kTheta;
-      const real kap = kappa_logderivs(th, lane, dl, d2l);
-      for (int c = 0; c < kTheta; ++c) S.J[lane * kTheta + c] = kap * dl[c];
-      S.kw[lane] = S.gnu[lane] * kap;
-    } else if (lane < 22) {
-      S.J[lane * kTheta + 21 + (lane - 20)] = 1.f;
-    } else if (lane == 22) {
-      real dS[3][3], d2S[3][3][3];
-      sigma_derivs(th, dS, d2S);
-      for (int e = 0; e < 3; ++e)
-        for (int c = 0; c < 3; ++c) S.J[(22 + e) * kTheta + 23 + c] = dS[e][c];
-      real h[3][3] = {{0.f}};
-      for (int e = 0; e < 3; ++e)
+    if (wid == 0) {
+      // Jacobian rows: flux moments (lanes 0..19), u, Sigma_s, rho
+      for (int e = lane; e < kNu * kTheta; e += 32) S.J[e] = 0.f;
+      __syncwarp();
+      if (lane < 20) {
+        real* dl = S.DL + lane * kTheta;
+        real* d2l = S.D2L + lane * kTheta;
+        const real kap = kappa_logderivs(th, lane, dl, d2l);
+        for (int c = 0; c < kTheta; ++c) S.J[lane * kTheta + c] = kap * dl[c];
+        S.kw[lane] = S.gnu[lane] * kap;
+      } else if (lane < 22) {
+        S.J[lane * kTheta + 21 + (lane - 20)] = 1.f;
+      } else if (lane == 22) {
+        real dS[3][3], d2S[3][3][3];
+        sigma_derivs(th, dS, d2S);
+        for (int e = 0; e < 3; ++e)
+          for (int c = 0; c < 3; ++c) S.J[(22 + e) * kTheta + 23 + c] = dS[e][c];
+        real h[3][3] = {{0.f}};
+        for (int e = 0; e < 3; ++e)
+          for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) h[c][d] += S.gnu[22 + e] * d2S[e][c][d];
         for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) h[c][d] += S.gnu[22 + e] * d2S[e][c][d];
-      for (int c = 0; c < 3; ++c)
-        for (int d = 0; d < 3; ++d) S.X[8 * 64 + c * 3 + d] = h[c][d];   // parked below
-    } else if (lane == 25) {
-      const real r = sigm(th[26]);
-      S.J[25 * kTheta + 26] = r * (1.f - r);
-    }
-    __syncwarp();
-    if (kMode == 2) {
-      // Sigma_s second-order chain term (parked by lane 22 past the KL scratch)
-      if (lane < 9) S.Hth[(23 + lane / 3) * kTheta + 23 + lane % 3] += S.X[8 * 64 + lane];
-      if (lane == 0) {
+          for (int d = 0; d < 3; ++d) S.X[8 * 64 + c * 3 + d] = h[c][d];   // parked below
+      } else if (lane == 25) {
         const real r = sigm(th[26]);
-        S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.f - r) * (1.f - 2.f * r);
+        S.J[25 * kTheta + 26] = r * (1.f - r);
       }
-    }
-    __syncwarp();
-    // gradient: J^T grad_nu over each column's rows
-    if (lane < kTheta) {
-      int rows[20];
-      const int nr = col_rows(lane, rows);
-      real gsum = 0.f;
-      for (int k = 0; k < nr; ++k) gsum = fmaf(S.J[rows[k] * kTheta + lane], S.gnu[rows[k]], gsum);
-      S.gth[lane] += gsum;
-    }
-    // X = H_nu J, only where J's column has support
-    for (int e = lane; e < (kMode == 2 ? kNu * kTheta : 0); e += 32) {
-      const int a = e / kTheta, c = e % kTheta;
-      int rows[20];
-      const int nr = col_rows(c, rows);
-      real x = 0.f;
-      for (int k = 0; k < nr; ++k) x = fmaf(S.Hnu[a * kNu + rows[k]], S.J[rows[k] * kTheta + c], x);
-      S.X[e] = x;
-    }
-    __syncwarp();
-    // Hth += J^T X (upper triangle, mirrored), plus the flux-moment
-    // second-order term sum_a kw_a (dl dl^T + diag d2l)
-    for (int e = lane; e < (kMode == 2 ? kTheta * kTheta : 0); e += 32) {
-      const int c = e / kTheta, d = e % kTheta;
-      if (d < c) continue;
-      int rows[20];
-      const int nr = col_rows(c, rows);
-      real x = 0.f;
-      for (int k = 0; k < nr; ++k) x = fmaf(S.J[rows[k] * kTheta + c], S.X[rows[k] * kTheta + d], x);
-      if (c <= 20 && d <= 20) {
-        for (int k = 0; k < nr; ++k) {
-          const int a = rows[k];
-          if (a >= 20) break;
-          x = fmaf(S.kw[a] * S.DL[a * kTheta + c], S.DL[a * kTheta + d], x);
-          if (c == d) x = fmaf(S.kw[a], S.D2L[a * kTheta + c], x);
+      __syncwarp();
+      if (kMode == 2) {
+        // Sigma_s second-order chain term (parked by lane 22 in X's space)
+        if (lane < 9) S.Hth[(23 + lane / 3) * kTheta + 23 + lane % 3] += S.X[8 * 64 + lane];
+        if (lane == 0) {
+          const real r = sigm(th[26]);
+          S.Hth[26 * kTheta + 26] += S.gnu[25] * r * (1.f - r) * (1.f - 2.f * r);
         }
       }
-      S.Hth[c * kTheta + d] += x;
-      if (d != c) S.Hth[d * kTheta + c] += x;
+      __syncwarp();
+      // gradient: J^T grad_nu over each column's rows
+      if (lane < kTheta) {
+        const int nr = nrows(lane);
+        real gsum = 0.f;
+        for (int k = 0; k < nr; ++k) {
+          const int a = rowof(lane, k);
+          gsum = fmaf(S.J[a * kTheta + lane], S.gnu[a], gsum);
+        }
+        S.gth[lane] += gsum;
+      }
     }
-    __syncwarp();
+    __syncthreads();
+    if (kMode == 2) {
+      // X = H_nu J, only where J's column has support
+      for (int e = tid; e < kNu * kTheta; e += kEpiThreads) {
+        const int a = e / kTheta, c = e % kTheta;
+        const int nr = nrows(c);
+        real x = 0.f;
+        for (int k = 0; k < nr; ++k) {
+          const int r = rowof(c, k);
+          x = fmaf(S.Hnu[a * kNu + r], S.J[r * kTheta + c], x);
+        }
+        S.X[e] = x;
+      }
+      __syncthreads();
+      // Hth += J^T X (upper triangle, mirrored), plus the flux-moment
+      // second-order term sum_a kw_a (dl dl^T + diag d2l)
+      for (int e = tid; e < kTheta * kTheta; e += kEpiThreads) {
+        const int c = e / kTheta, d = e % kTheta;
+        if (d < c) continue;
+        const int nr = nrows(c);
+        real x = 0.f;
+        for (int k = 0; k < nr; ++k) {
+          const int r = rowof(c, k);
+          x = fmaf(S.J[r * kTheta + c], S.X[r * kTheta + d], x);
+        }
+        if (c <= 20 && d <= 20) {
+          for (int k = 0; k < nr; ++k) {
+            const int a = rowof(c, k);
+            if (a >= 20) break;
+            x = fmaf(S.kw[a] * S.DL[a * kTheta + c], S.DL[a * kTheta + d], x);
+            if (c == d) x = fmaf(S.kw[a], S.D2L[a * kTheta + c], x);
+          }
+        }
+        S.Hth[c * kTheta + d] += x;
+        if (d != c) S.Hth[d * kTheta + c] += x;
+      }
+      __syncthreads();
+    }
   }
 
   const double Lrel = vrel - kl;
   const double Lfull = vbase + vrel - kl;
-  if (lane == 0) {
+  if (tid == 0) {
     if (elbo) elbo[j] = Lfull;
     if (elbo_rel) elbo_rel[j] = Lrel;
     // a non-finite value at a trial point is a rejected step, not an error
     if (!isfinite(Lfull) && !use_trial) set_error(v.err, CELESTE_DERR_NONFINITE);
   }
   if (kMode >= 1) {
-    bool bad = false;
-    for (int e = lane; e < kTheta; e += 32) {
+    int bad = 0;
+    for (int e = tid; e < kTheta; e += kEpiThreads) {
       grad_out[(size_t)j * kTheta + e] = (double)S.gth[e];
       bad |= !isfinite(S.gth[e]);
     }
-    for (int e = lane; e < (kMode == 2 ? kTheta * kTheta : 0); e += 32) {
+    for (int e = tid; e < (kMode == 2 ? kTheta * kTheta : 0); e += kEpiThreads) {
       hess_out[(size_t)j * kTheta * kTheta + e] = (double)S.Hth[e];
       bad |= !isfinite(S.Hth[e]);
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(v.err, CELESTE_DERR_NONFINITE);
+    if (__syncthreads_or(bad) && tid == 0) set_error(v.err, CELESTE_DERR_NONFINITE);
   }
 }
 
@@ -561,7 +579,7 @@ cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* 
                             double* elbo, double* elbo_rel, double* grad, double* hess) {
   if (v.n == 0) return cudaSuccess;
   set_smem_attr<2>();
-  epilogue_kernel<2><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
+  epilogue_kernel<2><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
                                                               hess, 0);
   return cudaGetLastError();
 }
@@ -570,7 +588,7 @@ cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const Model
                                  double* elbo, double* elbo_rel, double* grad) {
   if (v.n == 0) return cudaSuccess;
   set_smem_attr<1>();
-  epilogue_kernel<1><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
+  epilogue_kernel<1><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
                                                               nullptr, 0);
   return cudaGetLastError();
 }
@@ -579,7 +597,7 @@ cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const Mode
                                   double* elbo, double* elbo_rel, bool use_trial) {
   if (v.n == 0) return cudaSuccess;
   set_smem_attr<0>();
-  epilogue_kernel<0><<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, nullptr,
+  epilogue_kernel<0><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, nullptr,
                                                               nullptr, use_trial ? 1 : 0);
   return cudaGetLastError();
 }
