@@ -532,8 +532,8 @@ __device__ __forceinline__ double B_diag0(const TrSmem& S, double lam) { return 
 __device__ __forceinline__ double pivot_rcp(double d) {
   if (!(d > 0.0 && d < 1e300)) return 0.0;
   if (d > 1e-30 && d < 1e30) {
-    const double r = (double)__frcp_rn((float)d);
-    return fma(r, fma(-d, r, 1.0), r);
+    const double r = (double)__fdividef(1.f, (float)d);   // ~1e-7 seed
+    return fma(r, fma(-d, r, 1.0), r);                     // one Newton step: ~1e-14
   }
   return rcp64_any(d);
 }
@@ -663,21 +663,23 @@ __device__ void householder32(TrSmem& S) {
       for (; c < N; ++c) p0 = fmaf(r[c], vs[c], p0);
     }
     const float p = row ? bt * ((p0 + p1) + (p2 + p3)) : 0.f;
-    float K = v * p;
+    // K = v.p and v.g: two reductions with interleaved shuffle trees
+    float K = v * p, vg = v * gi;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) K += __shfl_xor_sync(0xffffffffu, K, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      K += __shfl_xor_sync(0xffffffffu, K, o);
+      vg += __shfl_xor_sync(0xffffffffu, vg, o);
+    }
     const float w = fmaf(-0.5f * bt * K, v, p);
     ws[lane] = w;
+    gi = fmaf(-bt * vg, v, gi);                   // g -= bt v (v.g)
     __syncwarp();
     if (row) {
       float* r = Bf + lane * N;
-      for (int c = k + 1; c < N; ++c) r[c] = fmaf(-v, ws[c], fmaf(-w, vs[c], r[c]));
+      int c = k + 1;
+#pragma unroll 4
+      for (; c < N; ++c) r[c] = fmaf(-v, ws[c], fmaf(-w, vs[c], r[c]));
     }
-    // g -= bt v (v.g)
-    float vg = v * gi;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vg += __shfl_xor_sync(0xffffffffu, vg, o);
-    gi = fmaf(-bt * vg, v, gi);
     __syncwarp();
   }
   if (lane == 0) {
