@@ -56,6 +56,7 @@ struct TrSmem {
   double lam_b;                    // boundary start when an interior try fails (0: none)
   int positive;                    // FP32 finds B positive definite
   int tried0;                      // l = 0 has been evaluated
+  int bisects;                     // bisection steps of the FP64 iteration
   float Bf[N * N];
   float betaf[32], dfr[32], efr[32], gfr[32];
   float cps[N * 32], gps[N * 32];  // per-lane scratch of the FP32 secular solves ([i][lane])
@@ -777,6 +778,7 @@ __device__ void locate32(TrSmem& S, double Delta) {
     S.lam = bracket ? sc * 0.5 * ((double)la + (double)lb) : 0.0;
     S.lam_b = S.lam;
     S.tried0 = 0;
+    S.bisects = 0;
     if (mode == 0) S.lam = 0.0;
     S.lo = -1.0;                      // FP64 bounds: none yet
     S.hi = -1.0;
@@ -825,14 +827,17 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
         // lo, a multiplier too small (indefinite, or |p| > Delta), < 0 for
         // none; hi, one large enough (|p| <= Delta), < 0 for none
         double lo = S.lo, hi = S.hi, next = lam;
-        int mode = S.mode, tried0 = S.tried0 | (lam == 0.0);
+        int mode = S.mode, tried0 = S.tried0 | (lam == 0.0), bisects = S.bisects;
         bool fin = false;
         if (!ok) {
           lo = fmax(lo, lam);
           if (mode == 0 && S.lam_b > lo && (hi < 0.0 || S.lam_b < hi)) {
             next = S.lam_b;
+          } else if (hi >= 0.0) {
+            next = 0.5 * (lo + hi);
+            ++bisects;
           } else {
-            next = hi >= 0.0 ? 0.5 * (lo + hi) : 2.0 * lam + 1e-12 * (1.0 + fabs(S.lmin_lo));
+            next = 2.0 * lam + 1e-12 * (1.0 + fabs(S.lmin_lo));
           }
           mode = 1;
         } else {
@@ -865,6 +870,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
                 next = 0.0;             // the root may be at 0: an interior step
               } else if (hi >= 0.0) {
                 next = 0.5 * (fmax(lo, 0.0) + hi);
+                ++bisects;
               } else {
                 next = 2.0 * lam + 1e-12 * (1.0 + fabs(S.lmin_lo));
               }
@@ -873,11 +879,16 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
           }
           mode = 1;
         }
+        // Bisecting again and again means the root hugs the pole (a nearly
+        // hard case, the multiplier within ~1e-10 of -lambda_min): the
+        // eigen-based all-FP64 path resolves it.
+        if (!fin && bisects >= 3) mode = 2;
         if (lane == 0) {
           S.lo = lo;
           S.hi = hi;
           S.lam = next;
           S.tried0 = tried0;
+          S.bisects = bisects;
           S.mode = fin ? 3 : mode;
         }
       }
