@@ -207,12 +207,14 @@ def cpu_baseline(problem, seconds, order=None):
 
 
 def derivs_source_hash(path):
-    """Hash of the derivative kernel's source: pixel.cu up to the next kernel
-    (its device helpers and derivs_kernel itself)."""
+    """Hash of the derivative kernel's source and build flags: pixel.cu up to
+    the next kernel (its device helpers and derivs_kernel itself)."""
     import hashlib
+    from paper_1803_00113_gb300 import build_lib
     text = open(path, "rb").read()
     cut = text.find(b"__global__ void __launch_bounds__(128) grad_kernel")
-    return hashlib.sha256(text[:cut if cut > 0 else len(text)]).hexdigest()[:16]
+    flags = " ".join(build_lib.FLAGS + build_lib.FILE_FLAGS.get("pixel.cu", [])).encode()
+    return hashlib.sha256(text[:cut if cut > 0 else len(text)] + flags).hexdigest()[:16]
 
 
 def traffic_per_launch(visits_per_launch):
