@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="serving: arrival window per rate")
     ap.add_argument("--pool", type=int, default=96, help="serving: distinct requests generated")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="serving: worker threads (0: the server's default)")
     ap.add_argument("--fo-max-steps", type=int, default=3000,
                     help="first-order comparison: step cap of the L-BFGS subsolver")
     ap.add_argument("--sources", type=int, default=0, help="override the source count")
@@ -67,8 +69,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick tile shapes per patch-size bucket before timing (default for batched)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default 256-pixel tiles instead of picking tile shapes per "
+                         "patch-size bucket before timing")
     ap.add_argument("--plain-sample", type=int, default=600,
                     help="sources timed in the plain one-source-per-launch form")
     return ap.parse_args(argv)
@@ -255,7 +258,7 @@ def run_ours(args):
         dp = cel.DeviceProblem(problem, dev, render_cache=dense and not args.no_cache)
         classes = cel.color_classes(problem)
         tiles = None
-        if args.autotune or args.workload == "batched":
+        if not args.no_autotune:
             from paper_1803_00113_gb300.autotune import autotune
             tiles, tune_report = autotune(ctx, dp, range(problem.n_sources))
             dp.set_theta(problem.theta)
@@ -628,7 +631,7 @@ def run_serving(args):
     def arrivals(rate, n):
         return np.cumsum(rng.exponential(1.0 / rate, n))
 
-    srv = cel.Server(model, device=local)
+    srv = cel.Server(model, device=local, workers=args.workers)
     _serve_run(cel, srv, pool[:8], np.zeros(8))          # warm-up: graphs, buffers
     clocks = ClockSampler(local)
     clocks.start()
@@ -665,7 +668,8 @@ def run_serving(args):
             "config": {"workload": "serving: Poisson arrivals at "
                                    f"{args.rates} requests/s, {args.serve_seconds:g} s each, "
                                    f"fits of <= 5 passes x <= 50 Newton iterations",
-                       "pool": args.pool, "l2": "inputs stream in per request (not reused)"},
+                       "pool": args.pool, "workers": args.workers or 2,
+                       "l2": "inputs stream in per request (not reused)"},
             "latency": per_rate,
             "plain_per_request": plain, "vs_plain": best["throughput"] / plain["throughput"],
             "e2e": {"value": best["throughput"], "unit": "fits/s",
