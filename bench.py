@@ -51,8 +51,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["field", "batched", "serving", "first-order"],
+    ap.add_argument("--workload", choices=["field", "batched", "serving", "first-order", "mcmc"],
                     default="field")
+    ap.add_argument("--mcmc-sources", type=int, default=4,
+                    help="mcmc: sources of the field sampled (the brightest)")
     ap.add_argument("--rates", default="50,200,500,1000,2000",
                     help="serving: Poisson arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
@@ -60,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--pool", type=int, default=96, help="serving: distinct requests generated")
     ap.add_argument("--workers", type=int, default=0,
                     help="serving: worker threads (0: the server's default)")
+    ap.add_argument("--serve-tile", type=int, default=128,
+                    help="serving: pixels per tile of the pixel kernels")
     ap.add_argument("--fo-max-steps", type=int, default=3000,
                     help="first-order comparison: step cap of the L-BFGS subsolver")
     ap.add_argument("--sources", type=int, default=0, help="override the source count")
@@ -631,7 +635,7 @@ def run_serving(args):
     def arrivals(rate, n):
         return np.cumsum(rng.exponential(1.0 / rate, n))
 
-    srv = cel.Server(model, device=local, workers=args.workers)
+    srv = cel.Server(model, device=local, workers=args.workers, pixels_per_item=args.serve_tile)
     _serve_run(cel, srv, pool[:8], np.zeros(8))          # warm-up: graphs, buffers
     clocks = ClockSampler(local)
     clocks.start()
@@ -649,7 +653,8 @@ def run_serving(args):
     st = srv.stats()
     srv.close()
     # the plain form: one request at a time, each its own fit, saturated
-    plain_srv = cel.Server(model, device=local, workers=1, max_batch=1)
+    plain_srv = cel.Server(model, device=local, workers=1, max_batch=1,
+                           pixels_per_item=args.serve_tile)
     _serve_run(cel, plain_srv, pool[:4], np.zeros(4))
     n_plain = min(len(pool), 48)
     res, wall = _serve_run(cel, plain_srv, pool[:n_plain], np.zeros(n_plain))
@@ -669,6 +674,7 @@ def run_serving(args):
                                    f"{args.rates} requests/s, {args.serve_seconds:g} s each, "
                                    f"fits of <= 5 passes x <= 50 Newton iterations",
                        "pool": args.pool, "workers": args.workers or 2,
+                       "pixels_per_tile": args.serve_tile,
                        "l2": "inputs stream in per request (not reused)"},
             "latency": per_rate,
             "plain_per_request": plain, "vs_plain": best["throughput"] / plain["throughput"],
@@ -773,10 +779,53 @@ def run_first_order(args):
             "e2e": None, "gpu_launches": int(ctx.launches())}
 
 
+# ---------------------------------------------------------------------------
+# the MCMC consumer: AIS + slice sampling per source (the paper's settings)
+# ---------------------------------------------------------------------------
+
+def run_mcmc(args):
+    """AIS (T = 200, N' = 25 per type) and B' = 25 slice-sampling sweeps for
+    the brightest sources of the field, neighbours fixed; every sampler
+    round is one batched log-likelihood call for all 50 chains."""
+    import torch
+    world, rank, local = dist_info()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    from paper_1803_00113_gb300 import build_lib
+    build_lib.build()
+    from paper_1803_00113_gb300 import mcmc
+    problem, cfg = workload("field", args.sources, SEED + 1)
+    bright = np.argsort(-problem.truth["logr"])[:args.mcmc_sources]
+    mcmc.type_posterior(problem, int(bright[0]), n_chains=4, T=2, B=1)   # warm-up
+    per, calls, correct, visits = [], 0, 0, 0
+    for s in bright:
+        s = int(s)
+        t0 = time.perf_counter()
+        r = mcmc.type_posterior(problem, s, n_chains=25, T=200, B=25, seed=s)
+        per.append(time.perf_counter() - t0)
+        calls += r["calls"]
+        visits += r["calls"] * 50 * problem.visits([s])
+        correct += int((r["p_star"] > 0.5) == bool(problem.truth["is_star"][s]))
+    total = sum(per)
+    return {"metric": "source posteriors/s (AIS T=200 x 25 chains per type + 25 sweeps)",
+            "value": len(per) / total, "unit": "sources/s", "n_gpus": 1, "steps": len(per),
+            "warmup": 1, "ms_per_step": 1e3 * total / len(per), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pixels, f64 sums",
+            "data": "synthetic (seeded field shaped like the paper's study set)",
+            "config": dict(cfg, workload=f"MCMC (AIS + slice sampling) of the {len(per)} brightest "
+                                         "field sources, neighbours fixed"),
+            "loglik_calls_per_s": calls / total, "visits_per_s": visits / total,
+            "seconds_per_source": per, "type_correct": correct,
+            "e2e": None, "gpu_launches": None}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         line = run_reference(args)
+    elif args.workload == "mcmc":
+        line = run_mcmc(args)
     elif args.workload == "first-order":
         line = run_first_order(args)
     elif args.workload == "serving":

@@ -239,6 +239,15 @@ int celeste_elbo_grad(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, 
 /* Value only (no derivatives): elbo[n] and elbo_rel[n] (either may be NULL). */
 int celeste_elbo(celeste_ctx* ctx, const celeste_plan* plan, double* elbo, double* elbo_rel);
 
+/* The pixel part of L_rel alone (no KL) for every source of the plan:
+ * out[n] (device, plan order) = sum over the source's patch pixels of the
+ * pixel term with the source minus the same sum without it.  With theta
+ * encoding point values (log-variances of -40, the type logit at +-40) this
+ * is log p(x | w_s, a_s, z_-s) - log p(x | source absent) of the Poisson
+ * likelihood (Eq. eq:log_p_last's V terms vanish), the quantity the AIS and
+ * slice-sampling MCMC of Sec. 3 evaluates for each proposal. */
+int celeste_loglik(celeste_ctx* ctx, const celeste_plan* plan, double* out);
+
 /* One trust-region Newton iteration (Sec. 4.3) on every source of the plan
  * whose status is not CONVERGED/FAILED/MAXITER: evaluate L_s, g, H at theta; solve
  * max g.p + p.H.p/2 s.t. |p| <= delta exactly in FP64; evaluate L_s at
@@ -370,7 +379,7 @@ typedef struct celeste_server_config {
   int32_t max_iter;
   double pass_tol;          /* nats per source */
   int32_t start_paused;     /* workers take no batch until celeste_server_pause(s, 0) */
-  int32_t reserved;
+  int32_t pixels_per_item;  /* tile size of the pixel kernels (0 = 256) */
 } celeste_server_config;
 
 /* One region: HOST arrays laid out as in celeste_problem (offsets, patch

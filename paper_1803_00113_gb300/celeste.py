@@ -46,7 +46,7 @@ class _ServerConfig(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("queue_bytes", ctypes.c_int64),
                 ("max_passes", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("pass_tol", ctypes.c_double), ("start_paused", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pixels_per_item", ctypes.c_int32)]
 
 
 class _Request(ctypes.Structure):
@@ -110,6 +110,7 @@ def lib():
         "celeste_elbo_grad_hess": (ctypes.c_int, [P, P, P, P, P, P]),
         "celeste_elbo": (ctypes.c_int, [P, P, P, P]),
         "celeste_elbo_grad": (ctypes.c_int, [P, P, P, P, P]),
+        "celeste_loglik": (ctypes.c_int, [P, P, P]),
         "celeste_newton_step": (ctypes.c_int, [P, P, P, P, P]),
         "celeste_tr_subproblem": (ctypes.c_int, [P, I32, P, P, P, P, P]),
         "celeste_render": (ctypes.c_int, [P, P, P, P]),
@@ -157,7 +158,8 @@ def exported_symbols():
     return ["celeste_create", "celeste_destroy", "celeste_synchronize", "celeste_launch_count",
             "celeste_profile_enable", "celeste_profile_read", "celeste_profile_kernels",
             "celeste_plan_create", "celeste_plan_destroy", "celeste_plan_visits",
-            "celeste_elbo_grad_hess", "celeste_elbo", "celeste_elbo_grad", "celeste_newton_step",
+            "celeste_elbo_grad_hess", "celeste_elbo", "celeste_elbo_grad", "celeste_loglik",
+            "celeste_newton_step",
             "celeste_tr_subproblem", "celeste_render", "celeste_background",
             "celeste_render_cache",
             "celeste_color_sources", "celeste_fit_create", "celeste_fit_destroy",
@@ -435,6 +437,14 @@ def elbo(plan: Plan):
     return e, er
 
 
+def loglik(plan: Plan, out: Optional[torch.Tensor] = None):
+    """Pixel part of L_rel (no KL) per plan source, float64 device tensor."""
+    if out is None:
+        out = torch.empty(plan.n, dtype=torch.float64, device=plan.ctx.device)
+    _check(lib().celeste_loglik(plan.ctx.handle, plan.handle, _ptr(out)), "celeste_loglik")
+    return out
+
+
 def newton_step(plan: Plan, delta: torch.Tensor, status: torch.Tensor,
                 elbo_rel: Optional[torch.Tensor] = None):
     """One trust-region iteration; delta/status are [n_sources] device tensors."""
@@ -628,12 +638,13 @@ class Server:
 
     def __init__(self, model, device: int = 0, workers: int = 2, max_batch: int = 0,
                  device_bytes: int = 0, queue_bytes: int = 0, max_passes: int = 5,
-                 max_iter: int = 50, pass_tol: float = 1e-3, start_paused: bool = False):
+                 max_iter: int = 50, pass_tol: float = 1e-3, start_paused: bool = False,
+                 pixels_per_item: int = 0):
         if not torch.cuda.is_available():
             raise CelesteError("no CUDA device: the library has no CPU path")
         self.model_struct = model_struct(model)
         cfg = _ServerConfig(workers, max_batch, device_bytes, queue_bytes, max_passes, max_iter,
-                            pass_tol, 1 if start_paused else 0, 0)
+                            pass_tol, 1 if start_paused else 0, pixels_per_item)
         h = ctypes.c_void_p()
         _check(lib().celeste_server_create(ctypes.byref(self.model_struct), device,
                                            ctypes.byref(cfg), ctypes.byref(h)),

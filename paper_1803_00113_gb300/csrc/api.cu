@@ -525,6 +525,18 @@ int celeste_elbo(celeste_ctx* c, const celeste_plan* pc, double* elbo, double* e
   }));
 }
 
+int celeste_loglik(celeste_ctx* c, const celeste_plan* pc, double* out) {
+  celeste_plan* p = const_cast<celeste_plan*>(pc);
+  if (!c || !p || p->ctx != c || !out) return CELESTE_EINVAL;
+  if (p->v.n == 0) return CELESTE_OK;
+  int rc = eval_common(c, p, false);
+  if (rc) return rc;
+  Launch L = make_launch(c, p);
+  ++c->launches;
+  return to_status(timed(c, CELESTE_K_EPILOGUE, 0, L.stream,
+                         [&] { return launch_epilogue_loglik(L, p->v, c->d_model, out); }));
+}
+
 int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, int32_t* status,
                         double* elbo_rel) {
   celeste_plan* p = const_cast<celeste_plan*>(pc);

@@ -349,7 +349,11 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (!v.active[j]) return;
   const int src = v.src_ids[j];
-  const double* thd = use_trial ? v.theta_trial + (size_t)j * kTheta : v.theta + (size_t)src * kTheta;
+  // use_trial: bit 0 evaluates theta_trial; bit 1 (value mode only) asks
+  // for the pixel part alone, without the KL (the log-likelihood of the
+  // source's point values relative to its absence)
+  const bool trial = (use_trial & 1) != 0, pixel_only = kMode == 0 && (use_trial & 2) != 0;
+  const double* thd = trial ? v.theta_trial + (size_t)j * kTheta : v.theta + (size_t)src * kTheta;
   if (tid < kTheta) S.th[tid] = (real)thd[tid];
   const real* th = S.th;
 
@@ -451,9 +455,9 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
     __syncthreads();
   }
 
-  if (wid == 0) kl_terms<kMode>(th, model, S, lane);
+  if (wid == 0 && !pixel_only) kl_terms<kMode>(th, model, S, lane);
   __syncthreads();
-  const double kl = (double)S.kls[0];
+  const double kl = pixel_only ? 0.0 : (double)S.kls[0];
   if (kMode >= 1) {
     if (wid == 0) {
       // Jacobian rows: flux moments (lanes 0..19), u, Sigma_s, rho
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
     if (elbo) elbo[j] = Lfull;
     if (elbo_rel) elbo_rel[j] = Lrel;
     // a non-finite value at a trial point is a rejected step, not an error
-    if (!isfinite(Lfull) && !use_trial) set_error(v.err, CELESTE_DERR_NONFINITE);
+    if (!isfinite(Lfull) && !trial) set_error(v.err, CELESTE_DERR_NONFINITE);
   }
   if (kMode >= 1) {
     int bad = 0;
@@ -599,6 +603,15 @@ cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const Mode
   set_smem_attr<0>();
   epilogue_kernel<0><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, nullptr,
                                                               nullptr, use_trial ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_loglik(const Launch& L, const PlanView& v, const ModelDev* model,
+                                   double* out) {
+  if (v.n == 0) return cudaSuccess;
+  set_smem_attr<0>();
+  epilogue_kernel<0><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, nullptr, out,
+                                                                      nullptr, nullptr, 2);
   return cudaGetLastError();
 }
 

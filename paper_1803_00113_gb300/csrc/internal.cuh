@@ -168,6 +168,9 @@ cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* 
                             double* elbo, double* elbo_rel, double* grad, double* hess);
 cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const ModelDev* model,
                                  double* elbo, double* elbo_rel, double* grad);
+// The pixel part of L_rel alone (no KL) into out[n].
+cudaError_t launch_epilogue_loglik(const Launch& L, const PlanView& v, const ModelDev* model,
+                                   double* out);
 cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
                                   double* elbo, double* elbo_rel, bool use_trial);
 // newton.cu

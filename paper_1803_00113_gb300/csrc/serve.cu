@@ -221,7 +221,9 @@ int run_batch(celeste_server* S, celeste_ctx* ctx, cudaStream_t stream,
   std::vector<int32_t> ids(n_src);
   for (int s = 0; s < n_src; ++s) ids[s] = s;
   celeste_fit* F = nullptr;
-  int rc = fit_create_segments(ctx, &P, ids.data(), n_src, seg_ptr.data(), R, nullptr, &F);
+  celeste_tuning tuning{};
+  tuning.pixels_per_item = S->cfg.pixels_per_item;
+  int rc = fit_create_segments(ctx, &P, ids.data(), n_src, seg_ptr.data(), R, &tuning, &F);
   if (rc) return rc;
   rc = fit_begin(ctx, F, S->cfg.max_passes, S->cfg.max_iter, S->cfg.pass_tol);
   std::vector<char> finished(R, 0);
@@ -376,7 +378,9 @@ int celeste_server_create(const celeste_model* model, int device, const celeste_
   if (S->cfg.device_bytes <= 0) S->cfg.device_bytes = (int64_t)4 << 30;
   if (S->cfg.queue_bytes <= 0) S->cfg.queue_bytes = 4 * S->cfg.device_bytes * S->cfg.workers;
   if (!(S->cfg.pass_tol >= 0.0) || S->cfg.max_passes < 0 || S->cfg.max_passes > 1000 ||
-      S->cfg.max_iter < 0 || S->cfg.max_iter > 1000 || S->cfg.workers > 64) {
+      S->cfg.max_iter < 0 || S->cfg.max_iter > 1000 || S->cfg.workers > 64 ||
+      (S->cfg.pixels_per_item != 0 &&
+       (S->cfg.pixels_per_item < 32 || S->cfg.pixels_per_item > 65536))) {
     delete S;
     return CELESTE_EINVAL;
   }
