@@ -132,21 +132,31 @@ def point_theta(W, kind: int, base):
     return th
 
 
-def replicate(problem, s: int, n: int):
-    """A problem holding source s's neighbours (fixed) and n copies of s.
-
-    Returns (problem, slice of the copies' source ids)."""
-    nbrs = [int(t) for t in problem.nbr_idx[problem.nbr_ptr[s]:problem.nbr_ptr[s + 1]]]
-    order = nbrs + [s] * n
-    pp, keep, nb, nbi = [0], [], [0], []
+def replicate(problem, sources, n: int):
+    """A problem holding the listed sources' neighbours (fixed, at their
+    theta) and n copies of each listed source.  A copy has its source's
+    patches and neighbours; copies are nobody's neighbours but their own
+    source's neighbours'.  Returns (problem, [slice of each source's copies])."""
+    sources = [int(s) for s in sources]
+    nbrs = []
+    for s in sources:
+        for t in problem.nbr_idx[problem.nbr_ptr[s]:problem.nbr_ptr[s + 1]]:
+            if int(t) not in nbrs:
+                nbrs.append(int(t))
     remap = {t: k for k, t in enumerate(nbrs)}
+    order = nbrs + [s for s in sources for _ in range(n)]
+    first = {t: [] for t in nbrs}                         # copies that see neighbour t
+    for c, s in enumerate(order[len(nbrs):]):
+        for t in problem.nbr_idx[problem.nbr_ptr[s]:problem.nbr_ptr[s + 1]]:
+            first[int(t)].append(len(nbrs) + c)
+    pp, keep, nb, nbi = [0], [], [0], []
     for k, t in enumerate(order):
         keep.extend(range(problem.patch_ptr[t], problem.patch_ptr[t + 1]))
         pp.append(len(keep))
         if k >= len(nbrs):
-            nbi.extend(remap[u] for u in nbrs)              # a copy sees s's neighbours
+            nbi.extend(remap[int(u)] for u in problem.nbr_idx[problem.nbr_ptr[t]:problem.nbr_ptr[t + 1]])
         else:
-            nbi.extend(len(nbrs) + c for c in range(n))     # a neighbour sees every copy
+            nbi.extend(first[t])
         nb.append(len(nbi))
     keep = np.asarray(keep, dtype=np.int64)
     out = dataclasses.replace(problem)
@@ -157,24 +167,27 @@ def replicate(problem, s: int, n: int):
     out.nbr_ptr = np.asarray(nb, dtype=np.int32)
     out.nbr_idx = np.asarray(nbi, dtype=np.int32)
     out.truth = None
-    return out, slice(len(nbrs), len(nbrs) + n)
+    base = len(nbrs)
+    return out, [slice(base + i * n, base + (i + 1) * n) for i in range(len(sources))]
 
 
 class GpuLogLik:
-    """log p(x | w, a) - log p(x | absent) for batches of (w, a) of one source."""
+    """log p(x | w, a) - log p(x | absent) for batches of point values of one
+    or several sources: n chains per source, one library call per batch."""
 
-    def __init__(self, problem, s: int, n: int, device: int = 0):
-        self.n = n
-        self.rep, self.sl = replicate(problem, s, n)
+    def __init__(self, problem, sources, n: int, device: int = 0):
+        sources = [int(sources)] if np.isscalar(sources) else [int(s) for s in sources]
+        self.n = n * len(sources)
+        self.rep, self.slices = replicate(problem, sources, n)
+        self.sl = slice(self.slices[0].start, self.slices[-1].stop)
         self.ctx = cel.Context(problem.model, device=device)
         self.dp = cel.DeviceProblem(self.rep, torch.device("cuda", device))
         self.plan = cel.Plan(self.ctx, self.dp, list(range(self.sl.start, self.sl.stop)))
-        self.base = np.asarray(problem.theta[s], dtype=np.float64)
-        self.out = torch.empty(n, dtype=torch.float64, device=self.ctx.device)
+        self.out = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
         self.calls = 0
 
     def __call__(self, thetas):
-        """thetas [n, 27] (point-value encodings) -> numpy [n]."""
+        """thetas [n_total, 27] (point-value encodings, copies in order) -> numpy."""
         self.dp.theta[self.sl] = torch.as_tensor(thetas, dtype=torch.float64,
                                                  device=self.ctx.device)
         cel.loglik(self.plan, self.out)
@@ -249,39 +262,39 @@ def slice_sweep(logp: Callable, W, lp, rng, widths, lo, hi, movable=None, m: int
 
 
 class JointTarget:
-    """Chains of several types in one state array: prior, bounds and the
-    batched log-likelihood of all chains at once."""
+    """Chains of several (source, type) groups in one state array: prior,
+    bounds and the batched log-likelihood of all chains at once.  groups:
+    list of (prior, kind, base theta, number of chains), in the row order
+    of the log-likelihood's copies."""
 
-    def __init__(self, priors, kinds, loglik_theta: Callable, base):
-        self.priors = priors
-        self.kinds = np.asarray(kinds)
-        self.d = max(p.dim for p in priors.values())
-        n = len(kinds)
-        self.lo = np.zeros((n, self.d))
-        self.hi = np.zeros((n, self.d))
+    def __init__(self, groups, loglik_theta: Callable):
+        self.groups = []
+        self.d = max(g[0].dim for g in groups)
+        n = sum(g[3] for g in groups)
+        self.lo = np.full((n, self.d), -np.inf)
+        self.hi = np.full((n, self.d), np.inf)
         self.movable = np.zeros((n, self.d), dtype=bool)
-        for kind, pr in priors.items():
-            r = self.kinds == kind
-            self.lo[r, :pr.dim] = pr.lo
-            self.hi[r, :pr.dim] = pr.hi
-            self.movable[r, :pr.dim] = True
-        self.lo[~self.movable] = -np.inf
-        self.hi[~self.movable] = np.inf
+        r0 = 0
+        for prior, kind, base, count in groups:
+            r = slice(r0, r0 + count)
+            self.lo[r, :prior.dim] = prior.lo
+            self.hi[r, :prior.dim] = prior.hi
+            self.movable[r, :prior.dim] = True
+            self.groups.append((prior, kind, np.asarray(base, dtype=np.float64), r))
+            r0 += count
+        self.n = n
         self.loglik_theta = loglik_theta
-        self.base = base
 
     def sample(self, rng):
-        W = np.zeros((len(self.kinds), self.d))
-        for kind, pr in self.priors.items():
-            r = self.kinds == kind
-            W[r, :pr.dim] = pr.sample(rng, int(r.sum()))
+        W = np.zeros((self.n, self.d))
+        for prior, _, _, r in self.groups:
+            W[r, :prior.dim] = prior.sample(rng, r.stop - r.start)
         return W
 
     def logprior(self, W):
         out = np.empty(W.shape[0])
-        for kind, pr in self.priors.items():
-            r = self.kinds == kind
-            out[r] = pr.logpdf(W[r, :pr.dim])
+        for prior, _, _, r in self.groups:
+            out[r] = prior.logpdf(W[r, :prior.dim])
         return out
 
     def loglik(self, W):
@@ -289,9 +302,8 @@ class JointTarget:
         # is never used) are clipped into it so that every encoding is finite
         W = np.clip(W, np.nextafter(self.lo, np.inf), np.nextafter(self.hi, -np.inf))
         th = np.empty((W.shape[0], fields.N_THETA))
-        for kind, pr in self.priors.items():
-            r = self.kinds == kind
-            th[r] = point_theta(W[r, :pr.dim], kind, self.base)
+        for prior, kind, base, r in self.groups:
+            th[r] = point_theta(W[r, :prior.dim], kind, base)
         return self.loglik_theta(th)
 
 
@@ -335,28 +347,40 @@ def log_mean_exp(a):
     return m + math.log(np.mean(np.exp(a - m)))
 
 
-def type_posterior(problem, s: int, n_chains: int = 25, T: int = 200, B: int = 25,
-                   seed: int = 0, device: int = 0, box: float = 2.0):
-    """AIS for both types of source s (N' = n_chains runs each, all chains
-    in lock step and every round one library call), then B slice-sampling
-    sweeps from the final states.  Returns a dict: p_star, log evidence and
-    samples per type, number of log-likelihood calls."""
+def type_posteriors(problem, sources, n_chains: int = 25, T: int = 200, B: int = 25,
+                    seed: int = 0, device: int = 0, box: float = 2.0):
+    """AIS for both types of each listed source (N' = n_chains runs per type,
+    neighbours fixed), then B slice-sampling sweeps from the final states;
+    all chains of all sources advance in lock step and every sampler round
+    is one library call.  Returns one dict per source: p_star, log evidence
+    and samples per type; and the number of log-likelihood calls."""
     rng = np.random.default_rng(seed)
-    u0 = problem.theta[s, fields.I_U:fields.I_U + 2]
-    priors = {STAR: Prior(problem.model, STAR, u0, box),
-              GALAXY: Prior(problem.model, GALAXY, u0, box)}
-    kinds = [STAR] * n_chains + [GALAXY] * n_chains
-    ev = GpuLogLik(problem, s, 2 * n_chains, device)
-    target = JointTarget(priors, kinds, ev, problem.theta[s])
+    sources = [int(s) for s in sources]
+    groups = []
+    for s in sources:
+        u0 = problem.theta[s, fields.I_U:fields.I_U + 2]
+        for kind in (STAR, GALAXY):
+            groups.append((Prior(problem.model, kind, u0, box), kind, problem.theta[s], n_chains))
+    ev = GpuLogLik(problem, sources, 2 * n_chains, device)
+    target = JointTarget(groups, ev)
     widths = np.full(target.d, 0.5)
     logw, W, samples = ais(target, T, rng, widths, B)
-    kinds = np.asarray(kinds)
-    out = {}
-    for kind in (STAR, GALAXY):
-        r = kinds == kind
-        out[kind] = dict(log_evidence=log_mean_exp(logw[r]), logw=logw[r],
-                         samples=samples[:, r, :priors[kind].dim].reshape(-1, priors[kind].dim))
-    la = math.log(problem.model.prior_a) + out[STAR]["log_evidence"]
-    lb = math.log(1.0 - problem.model.prior_a) + out[GALAXY]["log_evidence"]
-    p_star = 1.0 / (1.0 + math.exp(min(lb - la, 700.0)))
-    return dict(p_star=p_star, star=out[STAR], galaxy=out[GALAXY], calls=ev.calls)
+    results = []
+    for i, s in enumerate(sources):
+        res = {}
+        for prior, kind, _, r in target.groups[2 * i:2 * i + 2]:
+            res[kind] = dict(log_evidence=log_mean_exp(logw[r]), logw=logw[r],
+                             samples=samples[:, r, :prior.dim].reshape(-1, prior.dim))
+        la = math.log(problem.model.prior_a) + res[STAR]["log_evidence"]
+        lb = math.log(1.0 - problem.model.prior_a) + res[GALAXY]["log_evidence"]
+        p_star = 1.0 / (1.0 + math.exp(min(lb - la, 700.0)))
+        results.append(dict(source=s, p_star=p_star, star=res[STAR], galaxy=res[GALAXY]))
+    return results, ev.calls
+
+
+def type_posterior(problem, s: int, n_chains: int = 25, T: int = 200, B: int = 25,
+                   seed: int = 0, device: int = 0, box: float = 2.0):
+    """type_posteriors for one source; the dict also holds the call count."""
+    (r,), calls = type_posteriors(problem, [s], n_chains, T, B, seed, device, box)
+    r["calls"] = calls
+    return r

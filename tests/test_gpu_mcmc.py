@@ -55,3 +55,20 @@ def test_ais_picks_the_true_type_of_a_bright_source(mc, seed, star):
     # the position samples concentrate near the truth
     post = r["star" if star else "galaxy"]["samples"][:, 0:2].mean(0)
     assert np.all(np.abs(post - p.truth["pos"][0]) < 0.5), (post, p.truth["pos"][0])
+
+
+def test_several_sources_in_one_call_equal_one_at_a_time(mc):
+    p = fields.batched(seed=92, n_sources=8, min_side=15, max_side=31, max_images_per_band=2,
+                       max_neighbours=3)
+    srcs = [0, 3, 5]
+    rng = np.random.default_rng(3)
+    n = 4
+    rows = []
+    for s in srcs:
+        u0 = p.theta[s, fields.I_U:fields.I_U + 2]
+        W = mc.Prior(p.model, mc.GALAXY, u0, box=1.0).sample(rng, n)
+        rows.append(mc.point_theta(W, mc.GALAXY, p.theta[s]))
+    together = mc.GpuLogLik(p, srcs, n)(np.concatenate(rows))
+    for i, s in enumerate(srcs):
+        alone = mc.GpuLogLik(p, s, n)(rows[i])
+        assert np.array_equal(together[i * n:(i + 1) * n], alone), s
