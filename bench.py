@@ -156,21 +156,40 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.n0 = 0
+
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
+
+    def _wait_for(self, n, timeout=5.0):
+        t0 = time.time()
+        while self._lines() < n and time.time() - t0 < timeout and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first reading is
+        in, so that the readings bracket the timed region that follows."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.index)],
+                 "-lms", "50", "-i", str(self.index)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        self._wait_for(1)
+        self.n0 = self._lines()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._wait_for(self.n0 + 1)          # one reading after the timed region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
