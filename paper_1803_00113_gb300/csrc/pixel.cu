@@ -45,15 +45,23 @@ struct GalSums {
   float t4a, t4b, t4c, t4d, t4e;       // 1111, 1112, 1122, 1222, 2222
 };
 
-__device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, float px, float py,
+// The derivative kernel stages each galaxy component as 12 floats: the
+// precision and weight, then constants of the Hermite polynomials that do not
+// depend on the pixel.  Galaxy components of PSF component k share the star
+// component k's mean, so their offsets come from the star loop.
+constexpr int kGalF = 12;
+enum : int { G_P11 = 0, G_P12, G_P22, G_LW, G_TAU, G_2P12, G_M2P11S, G_M2P22S, G_M4P12, G_M2P12S };
+constexpr int kDerivRecF = kHdr + kPsf * kCompF + kPsf * 2 * kMaxProf * kGalF;
+
+__device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, float dx, float dy,
                                                GalSums& g) {
-  const Comp cc = load_comp(c);
-  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22, tau = cc.tau;
-  const float dx = px - cc.mx, dy = py - cc.my;
+  const float4 c0 = *reinterpret_cast<const float4*>(c);
+  const float4 c1 = *reinterpret_cast<const float4*>(c + 4);
+  const float2 c2 = *reinterpret_cast<const float2*>(c + 8);
+  const float P11 = c0.x, P12 = c0.y, P22 = c0.z, tau = c1.x, P12x2 = c1.y;
   const float y1 = fmaf(P11, dx, P12 * dy);
   const float y2 = fmaf(P12, dx, P22 * dy);
-  const float Q = fmaf(dx, y1, dy * y2);
-  const float phi = exp2f(fmaf(-kHalfLog2e, Q, cc.lw));
+  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c0.w));
   const float h11 = fmaf(y1, y1, -P11);
   const float h12 = fmaf(y1, y2, -P12);
   const float h22 = fmaf(y2, y2, -P22);
@@ -69,17 +77,18 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, floa
   g.t2xy = fmaf(pt, h12, g.t2xy);
   g.t2yy = fmaf(pt, h22, g.t2yy);
   // third order: y_a y_b y_c - (P_ab y_c + P_ac y_b + P_bc y_a)
-  const float P12x2 = 2.f * P12;
-  g.t3a = fmaf(pt, y1 * fmaf(-2.f, P11, h11), g.t3a);
-  g.t3b = fmaf(pt, fmaf(y2, h11, -P12x2 * y1), g.t3b);
-  g.t3c = fmaf(pt, fmaf(y1, h22, -P12x2 * y2), g.t3c);
-  g.t3d = fmaf(pt, y2 * fmaf(-2.f, P22, h22), g.t3d);
+  const float a1 = fmaf(-2.f, P11, h11), a2 = fmaf(-2.f, P22, h22);
+  const float py1 = pt * y1, py2 = pt * y2;
+  g.t3a = fmaf(py1, a1, g.t3a);
+  g.t3b = fmaf(py2, h11, fmaf(-P12x2, py1, g.t3b));
+  g.t3c = fmaf(py1, h22, fmaf(-P12x2, py2, g.t3c));
+  g.t3d = fmaf(py2, a2, g.t3d);
   // fourth order, written with h = y y^T - P
-  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), -2.f * P11 * P11), g.t4a);
-  g.t4b = fmaf(pt2, fmaf(h12, fmaf(-2.f, P11, h11), -P12x2 * (h11 + P11)), g.t4b);
-  g.t4c = fmaf(pt2, fmaf(h11, h22, -P12x2 * fmaf(2.f, h12, P12)), g.t4c);
-  g.t4d = fmaf(pt2, fmaf(h12, fmaf(-2.f, P22, h22), -P12x2 * (h22 + P22)), g.t4d);
-  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), -2.f * P22 * P22), g.t4e);
+  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), c1.z), g.t4a);
+  g.t4b = fmaf(pt2, fmaf(h12, a1, -P12x2 * (h11 + P11)), g.t4b);
+  g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, c2.x, c2.y)), g.t4c);
+  g.t4d = fmaf(pt2, fmaf(h12, a2, -P12x2 * (h22 + P22)), g.t4d);
+  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), c1.w), g.t4e);
 }
 
 __device__ __forceinline__ float gauss_value(const float* __restrict__ c, float px, float py) {
@@ -125,12 +134,15 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
                                              float* __restrict__ acc) {
   // ---- star: value, d mu, d mu d mu
   float F1 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+  float dxk[kPsf], dyk[kPsf];
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
     const float* c = rec + kHdr + k * kCompF;
     const Comp cc = load_comp(c);
     const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
     const float dx = px - cc.mx, dy = py - cc.my;
+    dxk[k] = dx;
+    dyk[k] = dy;
     const float y1 = fmaf(P11, dx, P12 * dy);
     const float y2 = fmaf(P12, dx, P22 * dy);
     const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
@@ -144,16 +156,18 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
   // ---- galaxy: exponential and de Vaucouleurs sums
   GalSums ge = {}, gd = {};
   const int per = ne + nd;
+#pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
+    const float* base = rec + kHdr + kPsf * kCompF + k * per * kGalF;
+    const float dx = dxk[k], dy = dyk[k];
     // the two profiles' sums are independent chains: interleave them
     const int nb = ne < nd ? ne : nd;
     for (int j = 0; j < nb; ++j) {
-      gal_accumulate(base + j * kCompF, px, py, ge);
-      gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
+      gal_accumulate(base + j * kGalF, dx, dy, ge);
+      gal_accumulate(base + (ne + j) * kGalF, dx, dy, gd);
     }
-    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kCompF, px, py, ge);
-    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kCompF, px, py, gd);
+    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kGalF, dx, dy, ge);
+    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kGalF, dx, dy, gd);
   }
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
@@ -394,19 +408,39 @@ __device__ __forceinline__ void stage_record(float* __restrict__ dst, const floa
   for (int i = lane; i < kRecF / 4; i += 32) d4[i] = s4[i];
 }
 
+// Stages a record in the derivative kernel's layout: header and star
+// components as they are, galaxy components expanded to kGalF floats.
+__device__ __forceinline__ void stage_record_derivs(float* __restrict__ dst,
+                                                    const float* __restrict__ src, int n_gal,
+                                                    int lane) {
+  constexpr int kHead4 = (kHdr + kPsf * kCompF) / 4;
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int i = lane; i < kHead4; i += 32) d4[i] = s4[i];
+  for (int ci = lane; ci < n_gal; ci += 32) {
+    const float4 a = s4[kHead4 + 2 * ci];
+    const float4 b = s4[kHead4 + 2 * ci + 1];
+    const float p11 = a.z, p12 = a.w, p22 = b.x;
+    float4* o = reinterpret_cast<float4*>(dst + kHdr + kPsf * kCompF + ci * kGalF);
+    o[0] = make_float4(p11, p12, p22, b.y);
+    o[1] = make_float4(b.z, 2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22);
+    o[2] = make_float4(-4.f * p12, -2.f * p12 * p12, 0.f, 0.f);
+  }
+}
+
 __global__ void __launch_bounds__(128) derivs_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kDerivRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record_derivs(rec, v.records + (size_t)item.pair * kRecF, kPsf * (ne + nd), lane);
     __syncwarp();
     float acc[kAcc];
 #pragma unroll
@@ -759,6 +793,7 @@ __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
 }
 
 static size_t smem_bytes(int wpb) { return (size_t)wpb * kRecF * sizeof(float); }
+static size_t smem_bytes_derivs(int wpb) { return (size_t)wpb * kDerivRecF * sizeof(float); }
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
@@ -769,7 +804,7 @@ static int g_occ[kOccKinds] = {0, 0, 0, 0, 0};
 cudaError_t init_pixel_occupancy() {
   const size_t sm = smem_bytes(kWpb);
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccDerivs], derivs_kernel,
-                                                                kWpb * 32, sm);
+                                                                kWpb * 32, smem_bytes_derivs(kWpb));
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccGrad], grad_kernel, kWpb * 32, sm);
   if (e == cudaSuccess)
@@ -802,7 +837,8 @@ cudaError_t launch_background(const Launch& L, const PlanView& v) {
 
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  derivs_kernel<<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  derivs_kernel<<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32, smem_bytes_derivs(kWpb),
+                  L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
