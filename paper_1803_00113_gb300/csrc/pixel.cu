@@ -24,15 +24,80 @@ namespace celeste {
 
 constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 
-// One Gaussian component of a staged record: two 16-byte shared-memory
-// loads (the record and each 8-float component are 16-byte aligned).
-struct Comp {
-  float mx, my, p11, p12, p22, lw, tau;
+// ---- staged records
+// Every pixel kernel stages the (source, image) record of its work item in
+// the warp's shared memory, built from the global record (8 floats per
+// component: mx, my, P11, P12, P22, lw, tau) in one of two layouts:
+//   value layout:  header | origins | each component {A11, A12, A22, lw}
+//   derivs layout: header | origins | star {A, lw | P, 0}
+//                                   | galaxy {A, lw | P, tau | Hermite constants}
+// A = -log2(e)/2 (P11, 2 P12, P22) are the coefficients of the exponent's
+// quadratic form: log2 phi = lw + A11 dx^2 + A12 dx dy + A22 dy^2.  Every
+// component convolved with PSF component k has that component's mean (the
+// source centre plus the PSF offset), so a kernel forms the pixel's offset
+// and its products once per k from the "origins".  Both layouts evaluate
+// phi with the same instructions: a value-only kernel and the derivative
+// kernel give bit-identical densities for the same record.
+constexpr int kOrgF = 8;                                   // (mx, my) per k, padded
+constexpr int kValF = 4;
+constexpr int kStarF = 8;
+constexpr int kGalF = 12;
+constexpr int kCompBase = kHdr + kOrgF;
+constexpr int kValRecF = kCompBase + kMaxComp * kValF;
+constexpr int kDerivRecF = kCompBase + kPsf * kStarF + kPsf * 2 * kMaxProf * kGalF;
+static_assert(2 * kPsf <= kOrgF && kValRecF % 4 == 0 && kDerivRecF % 4 == 0, "staged layout");
+
+__device__ __forceinline__ float4 quad_coeffs(float p11, float p12, float p22, float lw) {
+  return make_float4(-kHalfLog2e * p11, (-2.f * kHalfLog2e) * p12, -kHalfLog2e * p22, lw);
+}
+
+// Stages the record at src (global) into dst (the warp's shared memory);
+// n_comp = kPsf (1 + n_exp + n_dev) components in the global order (stars,
+// then per PSF component the exponential and de Vaucouleurs components).
+template <bool kDerivs>
+__device__ __forceinline__ void stage_record(float* __restrict__ dst, const float* __restrict__ src,
+                                             int n_comp, int lane) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  if (lane < kHdr / 4) d4[lane] = s4[lane];
+  if (lane < kPsf)
+    *reinterpret_cast<float2*>(dst + kHdr + 2 * lane) =
+        *reinterpret_cast<const float2*>(src + kHdr + lane * kCompF);
+  for (int ci = lane; ci < n_comp; ci += 32) {
+    const float4 a = s4[kHdr / 4 + 2 * ci];
+    const float4 b = s4[kHdr / 4 + 2 * ci + 1];
+    const float p11 = a.z, p12 = a.w, p22 = b.x;
+    const float4 q = quad_coeffs(p11, p12, p22, b.y);
+    if (!kDerivs) {
+      d4[kCompBase / 4 + ci] = q;
+    } else if (ci < kPsf) {
+      float4* o = reinterpret_cast<float4*>(dst + kCompBase + ci * kStarF);
+      o[0] = q;
+      o[1] = make_float4(p11, p12, p22, 0.f);
+    } else {
+      float4* o = reinterpret_cast<float4*>(dst + kCompBase + kPsf * kStarF + (ci - kPsf) * kGalF);
+      o[0] = q;
+      o[1] = make_float4(p11, p12, p22, b.z);
+      o[2] = make_float4(2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22, -2.f * p12 * p12);
+    }
+  }
+}
+
+// A pixel's offset from PSF component k's mean, and its products.
+struct Offset {
+  float dx, dy, xx, xy, yy;
 };
-__device__ __forceinline__ Comp load_comp(const float* __restrict__ c) {
-  const float4 a = *reinterpret_cast<const float4*>(c);
-  const float4 b = *reinterpret_cast<const float4*>(c + 4);
-  return Comp{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+__device__ __forceinline__ float2 pixel_delta(const float* __restrict__ rec, int k, float px,
+                                              float py) {
+  const float2 m = *reinterpret_cast<const float2*>(rec + kHdr + 2 * k);
+  return make_float2(px - m.x, py - m.y);
+}
+__device__ __forceinline__ Offset make_offset(float2 d) {
+  return Offset{d.x, d.y, d.x * d.x, d.x * d.y, d.y * d.y};
+}
+// Density (weight and normaliser included) of a component with coefficients q.
+__device__ __forceinline__ float gauss_density(const float4 q, const Offset& o) {
+  return exp2f(fmaf(q.x, o.xx, fmaf(q.y, o.xy, fmaf(q.z, o.yy, q.w))));
 }
 
 // Sums over the components of one galaxy profile (weights without rho):
@@ -45,23 +110,17 @@ struct GalSums {
   float t4a, t4b, t4c, t4d, t4e;       // 1111, 1112, 1122, 1222, 2222
 };
 
-// The derivative kernel stages each galaxy component as 12 floats: the
-// precision and weight, then constants of the Hermite polynomials that do not
-// depend on the pixel.  Galaxy components of PSF component k share the star
-// component k's mean, so their offsets come from the star loop.
-constexpr int kGalF = 12;
-enum : int { G_P11 = 0, G_P12, G_P22, G_LW, G_TAU, G_2P12, G_M2P11S, G_M2P22S, G_M4P12, G_M2P12S };
-constexpr int kDerivRecF = kHdr + kPsf * kCompF + kPsf * 2 * kMaxProf * kGalF;
-
-__device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, float dx, float dy,
+// One galaxy component of the derivs layout: its 12 floats are
+// {A, lw | P11, P12, P22, tau | 2 P12, -2 P11^2, -2 P22^2, -2 P12^2}.
+__device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, const Offset& o,
                                                GalSums& g) {
-  const float4 c0 = *reinterpret_cast<const float4*>(c);
-  const float4 c1 = *reinterpret_cast<const float4*>(c + 4);
-  const float2 c2 = *reinterpret_cast<const float2*>(c + 8);
-  const float P11 = c0.x, P12 = c0.y, P22 = c0.z, tau = c1.x, P12x2 = c1.y;
-  const float y1 = fmaf(P11, dx, P12 * dy);
-  const float y2 = fmaf(P12, dx, P22 * dy);
-  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), c0.w));
+  const float4 q = *reinterpret_cast<const float4*>(c);
+  const float4 pp = *reinterpret_cast<const float4*>(c + 4);
+  const float4 hc = *reinterpret_cast<const float4*>(c + 8);
+  const float P11 = pp.x, P12 = pp.y, P22 = pp.z, tau = pp.w, P12x2 = hc.x;
+  const float y1 = fmaf(P11, o.dx, P12 * o.dy);
+  const float y2 = fmaf(P12, o.dx, P22 * o.dy);
+  const float phi = gauss_density(q, o);
   const float h11 = fmaf(y1, y1, -P11);
   const float h12 = fmaf(y1, y2, -P12);
   const float h22 = fmaf(y2, y2, -P22);
@@ -84,34 +143,33 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, floa
   g.t3c = fmaf(py1, h22, fmaf(-P12x2, py2, g.t3c));
   g.t3d = fmaf(py2, a2, g.t3d);
   // fourth order, written with h = y y^T - P
-  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), c1.z), g.t4a);
+  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), hc.y), g.t4a);
   g.t4b = fmaf(pt2, fmaf(h12, a1, -P12x2 * (h11 + P11)), g.t4b);
-  g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, c2.x, c2.y)), g.t4c);
+  g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, -2.f * P12x2, hc.w)), g.t4c);
   g.t4d = fmaf(pt2, fmaf(h12, a2, -P12x2 * (h22 + P22)), g.t4d);
-  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), c1.w), g.t4e);
+  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), hc.z), g.t4e);
 }
 
-__device__ __forceinline__ float gauss_value(const float* __restrict__ c, float px, float py) {
-  const Comp cc = load_comp(c);
-  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
-  const float dx = px - cc.mx, dy = py - cc.my;
-  const float y1 = fmaf(P11, dx, P12 * dy);
-  const float y2 = fmaf(P12, dx, P22 * dy);
-  const float Q = fmaf(dx, y1, dy * y2);
-  return exp2f(fmaf(-kHalfLog2e, Q, cc.lw));
-}
-
-// Galaxy (rho-mixed) and star profile densities of one pair at a pixel.
+// Galaxy (rho-mixed) and star profile densities of one pair at a pixel
+// (value layout).
 __device__ __forceinline__ void profiles_value(const float* __restrict__ rec, int ne, int nd,
                                                float px, float py, float& F0, float& F1) {
+  const float4* q4 = reinterpret_cast<const float4*>(rec + kCompBase);
   float fs = 0.f, fe = 0.f, fd = 0.f;
-#pragma unroll
-  for (int k = 0; k < kPsf; ++k) fs += gauss_value(rec + kHdr + k * kCompF, px, py);
   const int per = ne + nd;
+  const int nb = ne < nd ? ne : nd;
+#pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
-    for (int j = 0; j < ne; ++j) fe += gauss_value(base + j * kCompF, px, py);
-    for (int j = 0; j < nd; ++j) fd += gauss_value(base + (ne + j) * kCompF, px, py);
+    const Offset o = make_offset(pixel_delta(rec, k, px, py));
+    fs += gauss_density(q4[k], o);
+    const float4* g = q4 + kPsf + k * per;
+    // the two profiles' sums are independent chains: interleave them
+    for (int j = 0; j < nb; ++j) {
+      fe += gauss_density(g[j], o);
+      fd += gauss_density(g[ne + j], o);
+    }
+    for (int j = nb; j < ne; ++j) fe += gauss_density(g[j], o);
+    for (int j = nb; j < nd; ++j) fd += gauss_density(g[ne + j], o);
   }
   F0 = fmaf(rec[H_RHO], fe, rec[H_RHO1] * fd);
   F1 = fs;
@@ -134,40 +192,39 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
                                              float* __restrict__ acc) {
   // ---- star: value, d mu, d mu d mu
   float F1 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-  float dxk[kPsf], dyk[kPsf];
+  float2 dk[kPsf];
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* c = rec + kHdr + k * kCompF;
-    const Comp cc = load_comp(c);
-    const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
-    const float dx = px - cc.mx, dy = py - cc.my;
-    dxk[k] = dx;
-    dyk[k] = dy;
-    const float y1 = fmaf(P11, dx, P12 * dy);
-    const float y2 = fmaf(P12, dx, P22 * dy);
-    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
+    dk[k] = pixel_delta(rec, k, px, py);
+    const Offset o = make_offset(dk[k]);
+    const float* c = rec + kCompBase + k * kStarF;
+    const float4 q = *reinterpret_cast<const float4*>(c);
+    const float4 pp = *reinterpret_cast<const float4*>(c + 4);
+    const float y1 = fmaf(pp.x, o.dx, pp.y * o.dy);
+    const float y2 = fmaf(pp.y, o.dx, pp.z * o.dy);
+    const float phi = gauss_density(q, o);
     F1 += phi;
     sx = fmaf(phi, y1, sx);
     sy = fmaf(phi, y2, sy);
-    sxx = fmaf(phi, fmaf(y1, y1, -P11), sxx);
-    sxy = fmaf(phi, fmaf(y1, y2, -P12), sxy);
-    syy = fmaf(phi, fmaf(y2, y2, -P22), syy);
+    sxx = fmaf(phi, fmaf(y1, y1, -pp.x), sxx);
+    sxy = fmaf(phi, fmaf(y1, y2, -pp.y), sxy);
+    syy = fmaf(phi, fmaf(y2, y2, -pp.z), syy);
   }
   // ---- galaxy: exponential and de Vaucouleurs sums
   GalSums ge = {}, gd = {};
   const int per = ne + nd;
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* base = rec + kHdr + kPsf * kCompF + k * per * kGalF;
-    const float dx = dxk[k], dy = dyk[k];
+    const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
+    const Offset o = make_offset(dk[k]);
     // the two profiles' sums are independent chains: interleave them
     const int nb = ne < nd ? ne : nd;
     for (int j = 0; j < nb; ++j) {
-      gal_accumulate(base + j * kGalF, dx, dy, ge);
-      gal_accumulate(base + (ne + j) * kGalF, dx, dy, gd);
+      gal_accumulate(base + j * kGalF, o, ge);
+      gal_accumulate(base + (ne + j) * kGalF, o, gd);
     }
-    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kGalF, dx, dy, ge);
-    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kGalF, dx, dy, gd);
+    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kGalF, o, ge);
+    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kGalF, o, gd);
   }
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
@@ -304,15 +361,15 @@ struct GalSums1 {
   float s0, s1x, s1y, t2xx, t2xy, t2yy;
 };
 
-__device__ __forceinline__ void gal_accumulate1(const float* __restrict__ c, float px, float py,
+__device__ __forceinline__ void gal_accumulate1(const float* __restrict__ c, const Offset& o,
                                                 GalSums1& g) {
-  const Comp cc = load_comp(c);
-  const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
-  const float dx = px - cc.mx, dy = py - cc.my;
-  const float y1 = fmaf(P11, dx, P12 * dy);
-  const float y2 = fmaf(P12, dx, P22 * dy);
-  const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
-  const float pt = phi * cc.tau;
+  const float4 q = *reinterpret_cast<const float4*>(c);
+  const float4 pp = *reinterpret_cast<const float4*>(c + 4);
+  const float P11 = pp.x, P12 = pp.y, P22 = pp.z;
+  const float y1 = fmaf(P11, o.dx, P12 * o.dy);
+  const float y2 = fmaf(P12, o.dx, P22 * o.dy);
+  const float phi = gauss_density(q, o);
+  const float pt = phi * pp.w;
   g.s0 += phi;
   g.s1x = fmaf(phi, y1, g.s1x);
   g.s1y = fmaf(phi, y2, g.s1y);
@@ -327,30 +384,34 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
                                            float px, float py, float x, float2 bg,
                                            float* __restrict__ acc) {
   float F1 = 0.f, sx = 0.f, sy = 0.f;
+  float2 dk[kPsf];
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* c = rec + kHdr + k * kCompF;
-    const Comp cc = load_comp(c);
-    const float P11 = cc.p11, P12 = cc.p12, P22 = cc.p22;
-    const float dx = px - cc.mx, dy = py - cc.my;
-    const float y1 = fmaf(P11, dx, P12 * dy);
-    const float y2 = fmaf(P12, dx, P22 * dy);
-    const float phi = exp2f(fmaf(-kHalfLog2e, fmaf(dx, y1, dy * y2), cc.lw));
+    dk[k] = pixel_delta(rec, k, px, py);
+    const Offset o = make_offset(dk[k]);
+    const float* c = rec + kCompBase + k * kStarF;
+    const float4 q = *reinterpret_cast<const float4*>(c);
+    const float4 pp = *reinterpret_cast<const float4*>(c + 4);
+    const float y1 = fmaf(pp.x, o.dx, pp.y * o.dy);
+    const float y2 = fmaf(pp.y, o.dx, pp.z * o.dy);
+    const float phi = gauss_density(q, o);
     F1 += phi;
     sx = fmaf(phi, y1, sx);
     sy = fmaf(phi, y2, sy);
   }
   GalSums1 ge = {}, gd = {};
   const int per = ne + nd;
+#pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    const float* base = rec + kHdr + (kPsf + k * per) * kCompF;
+    const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
+    const Offset o = make_offset(dk[k]);
     const int nb = ne < nd ? ne : nd;
     for (int j = 0; j < nb; ++j) {
-      gal_accumulate1(base + j * kCompF, px, py, ge);
-      gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
+      gal_accumulate1(base + j * kGalF, o, ge);
+      gal_accumulate1(base + (ne + j) * kGalF, o, gd);
     }
-    for (int j = nb; j < ne; ++j) gal_accumulate1(base + j * kCompF, px, py, ge);
-    for (int j = nb; j < nd; ++j) gal_accumulate1(base + (ne + j) * kCompF, px, py, gd);
+    for (int j = nb; j < ne; ++j) gal_accumulate1(base + j * kGalF, o, ge);
+    for (int j = nb; j < nd; ++j) gal_accumulate1(base + (ne + j) * kGalF, o, gd);
   }
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
@@ -401,34 +462,9 @@ __device__ __forceinline__ void reduce_store(float* __restrict__ acc, float* __r
     if ((a & 31) == lane) out[a] = acc[a];
 }
 
-__device__ __forceinline__ void stage_record(float* __restrict__ dst, const float* __restrict__ src,
-                                             int lane) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* d4 = reinterpret_cast<float4*>(dst);
-  for (int i = lane; i < kRecF / 4; i += 32) d4[i] = s4[i];
-}
-
-// Stages a record in the derivative kernel's layout: header and star
-// components as they are, galaxy components expanded to kGalF floats.
-__device__ __forceinline__ void stage_record_derivs(float* __restrict__ dst,
-                                                    const float* __restrict__ src, int n_gal,
-                                                    int lane) {
-  constexpr int kHead4 = (kHdr + kPsf * kCompF) / 4;
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* d4 = reinterpret_cast<float4*>(dst);
-  for (int i = lane; i < kHead4; i += 32) d4[i] = s4[i];
-  for (int ci = lane; ci < n_gal; ci += 32) {
-    const float4 a = s4[kHead4 + 2 * ci];
-    const float4 b = s4[kHead4 + 2 * ci + 1];
-    const float p11 = a.z, p12 = a.w, p22 = b.x;
-    float4* o = reinterpret_cast<float4*>(dst + kHdr + kPsf * kCompF + ci * kGalF);
-    o[0] = make_float4(p11, p12, p22, b.y);
-    o[1] = make_float4(b.z, 2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22);
-    o[2] = make_float4(-4.f * p12, -2.f * p12 * p12, 0.f, 0.f);
-  }
-}
-
-__global__ void __launch_bounds__(128) derivs_kernel(PlanView v, int ne, int nd) {
+// Three blocks per SM (168 registers a thread) keep 12 warps resident; the
+// few registers this costs spill outside the pixel loop.
+__global__ void __launch_bounds__(128, 3) derivs_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
@@ -440,7 +476,8 @@ __global__ void __launch_bounds__(128) derivs_kernel(PlanView v, int ne, int nd)
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
     __syncwarp();
-    stage_record_derivs(rec, v.records + (size_t)item.pair * kRecF, kPsf * (ne + nd), lane);
+    stage_record<true>(rec, v.records + (size_t)item.pair * kRecF,
+                       kPsf * (1 + ne + nd), lane);
     __syncwarp();
     float acc[kAcc];
 #pragma unroll
@@ -462,14 +499,15 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kDerivRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record<true>(rec, v.records + (size_t)item.pair * kRecF,
+                       kPsf * (1 + ne + nd), lane);
     __syncwarp();
     float acc[kGradAcc];
 #pragma unroll
@@ -497,14 +535,15 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kValRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
+                        kPsf * (1 + ne + nd), lane);
     __syncwarp();
     float rel = 0.f, base = 0.f;
     const int end = item.start + item.count;
@@ -538,7 +577,7 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kValRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
@@ -590,7 +629,8 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
       const int np = v.pair_nbr[nb];
       const PairInfo qn = v.pairs[np];
       __syncwarp();
-      stage_record(rec, v.records + (size_t)np * kRecF, lane);
+      stage_record<false>(rec, v.records + (size_t)np * kRecF,
+                          kPsf * (1 + ne + nd), lane);
       __syncwarp();
       for (int q = item.start + lane; q < end; q += 32) {
         const int qy = q / pi.w;
@@ -617,14 +657,15 @@ __global__ void __launch_bounds__(128) render_kernel(PlanView v, int ne, int nd,
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kValRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     const int64_t off = patches[pi.patch].pool_offset;
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
+                        kPsf * (1 + ne + nd), lane);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -646,7 +687,7 @@ __global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, i
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kValRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
@@ -654,7 +695,8 @@ __global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, i
     if (status && status[pi.source] != CELESTE_ST_ACCEPTED) continue;
     float2* out = v.cache + v.patches[pi.patch].pool_offset;
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
+                        kPsf * (1 + ne + nd), lane);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -690,13 +732,14 @@ __global__ void __launch_bounds__(128) accumulate_kernel(PlanView v, int ne, int
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kRecF;
+  float* rec = smem + wib * kValRecF;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     __syncwarp();
-    stage_record(rec, v.records + (size_t)item.pair * kRecF, lane);
+    stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
+                        kPsf * (1 + ne + nd), lane);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -792,7 +835,7 @@ __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
   }
 }
 
-static size_t smem_bytes(int wpb) { return (size_t)wpb * kRecF * sizeof(float); }
+static size_t smem_bytes(int wpb) { return (size_t)wpb * kValRecF * sizeof(float); }
 static size_t smem_bytes_derivs(int wpb) { return (size_t)wpb * kDerivRecF * sizeof(float); }
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
@@ -806,7 +849,8 @@ cudaError_t init_pixel_occupancy() {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccDerivs], derivs_kernel,
                                                                 kWpb * 32, smem_bytes_derivs(kWpb));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccGrad], grad_kernel, kWpb * 32, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccGrad], grad_kernel, kWpb * 32,
+                                                       smem_bytes_derivs(kWpb));
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccValue], value_kernel, kWpb * 32, sm);
   if (e == cudaSuccess)
@@ -845,7 +889,8 @@ cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
 
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
+  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes_derivs(kWpb),
+                L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
