@@ -38,9 +38,13 @@ METRIC = "source-pixel visits/s (ELBO+grad+Hessian)"
 UNIT = "visits/s"
 # Algorithmic FP32 work of one visit in the derivative pixel kernel (value,
 # 10 first and 52 second derivatives over the per-image natural coordinates,
-# 48 galaxy + 3 star Gaussian components; FMA = 2 FLOP), counted from the
-# kernel's arithmetic as written.
+# 48 galaxy + 3 star Gaussian components; FMA = 2 FLOP), counted on the
+# direct formulation: every component's Hermite polynomials from its own
+# offset and precision.  The kernel shares the offsets of the components of
+# one PSF component and stages pixel-independent constants, and executes
+# EXECUTED_FLOP_PER_VISIT; the roofline reports both fractions.
 FLOP_PER_VISIT = 5320
+EXECUTED_FLOP_PER_VISIT = 4771
 FP32_LANES_PER_SM = 128
 SEED = 1803_00113
 
@@ -76,6 +80,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default 256-pixel tiles instead of picking tile shapes per "
                          "patch-size bucket before timing")
+    ap.add_argument("--tiles", default=None,
+                    help="pixels per work item for the four patch-area buckets, comma-separated "
+                         "(0 = default); replaces the autotuner")
     ap.add_argument("--plain-sample", type=int, default=600,
                     help="sources timed in the plain one-source-per-launch form")
     return ap.parse_args(argv)
@@ -281,9 +288,14 @@ def run_ours(args):
         dp = cel.DeviceProblem(problem, dev, render_cache=dense and not args.no_cache)
         classes = cel.color_classes(problem)
         tiles = None
-        if not args.no_autotune:
+        if args.tiles:
+            tiles = [int(t) for t in args.tiles.split(",")]
+            if len(tiles) != 4 or any(t < 0 for t in tiles):
+                raise SystemExit("--tiles wants four non-negative integers")
+        elif not args.no_autotune:
             from paper_1803_00113_gb300.autotune import autotune
-            tiles, tune_report = autotune(ctx, dp, range(problem.n_sources))
+            tiles, tune_report = autotune(ctx, dp, range(problem.n_sources), reps=2,
+                                          groups=classes)
             dp.set_theta(problem.theta)
         plans = [cel.Plan(ctx, dp, c, ppi_bucket=tiles) for c in classes]
         visits = sum(p.visits for p in plans)
@@ -492,6 +504,9 @@ def run_ours(args):
                        graph=graph is not None, visits_per_step=visits,
                        colour_classes=len(classes),
                        tiles_per_area_bucket=tiles or [256, 256, 256, 256],
+                       tile_tuning=("given (--tiles)" if args.tiles else
+                                    "composed: the step's colour-class plans, every kernel timed"
+                                    if tiles else "default 256 pixels per item"),
                        render_cache=dp.cache is not None),
         "grad_vs_hess": ratio,
         "kernels_one_step": breakdown,
@@ -507,6 +522,9 @@ def run_ours(args):
                      "traffic": traffic, "kernel": "derivs_kernel",
                      "kernel_ms_per_launch": avg_ms, "visits_per_launch": per_launch_visits,
                      "flop_per_visit": FLOP_PER_VISIT,
+                     "executed_flop_per_visit": EXECUTED_FLOP_PER_VISIT,
+                     "frac_executed": (achieved / peak * EXECUTED_FLOP_PER_VISIT / FLOP_PER_VISIT)
+                     if achieved else None,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                    f"lanes x 2 FLOP x {sm_max:.0f} MHz"},
         "plain_per_source": plain,

@@ -192,11 +192,9 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
                                              float* __restrict__ acc) {
   // ---- star: value, d mu, d mu d mu
   float F1 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-  float2 dk[kPsf];
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
-    dk[k] = pixel_delta(rec, k, px, py);
-    const Offset o = make_offset(dk[k]);
+    const Offset o = make_offset(pixel_delta(rec, k, px, py));
     const float* c = rec + kCompBase + k * kStarF;
     const float4 q = *reinterpret_cast<const float4*>(c);
     const float4 pp = *reinterpret_cast<const float4*>(c + 4);
@@ -213,10 +211,12 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
   // ---- galaxy: exponential and de Vaucouleurs sums
   GalSums ge = {}, gd = {};
   const int per = ne + nd;
-#pragma unroll
+  // kept rolled: three copies of this loop cost more in instruction fetch
+  // than recomputing the offsets
+#pragma unroll 1
   for (int k = 0; k < kPsf; ++k) {
     const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
-    const Offset o = make_offset(dk[k]);
+    const Offset o = make_offset(pixel_delta(rec, k, px, py));
     // the two profiles' sums are independent chains: interleave them
     const int nb = ne < nd ? ne : nd;
     for (int j = 0; j < nb; ++j) {

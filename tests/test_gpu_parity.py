@@ -279,3 +279,26 @@ def test_autotuned_tiles_give_the_same_results(cel):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         # only the FP32 summation order differs between tilings
         assert np.all(np.abs(a - b) <= 1e-5 * np.abs(b) + 1e-6 * np.abs(b).max())
+
+
+def test_composed_autotune_over_colour_classes(cel):
+    """The composed mode times the step's own plans (the colour classes) and
+    only touches buckets that hold sources."""
+    p = fields.batched(seed=13, n_sources=24, min_side=15, max_side=101, max_images_per_band=2,
+                       max_neighbours=3)
+    ctx = _ctx(cel, p)
+    dp = cel.DeviceProblem(p, render_cache=True)
+    classes = cel.color_classes(p)
+    from paper_1803_00113_gb300.autotune import autotune, source_bucket
+    tiles, report = autotune(ctx, dp, range(p.n_sources), candidates=(64, 256), reps=1,
+                             groups=classes)
+    used = {source_bucket(p, s) for s in range(p.n_sources)}
+    for b in range(4):
+        assert tiles[b] in ((64, 256) if b in used else (0,))
+    assert all(v > 0 for v in report["composed_ms"].values())
+    ref = cel.elbo_grad_hess(cel.Plan(ctx, dp, list(range(p.n_sources))))
+    got = cel.elbo_grad_hess(cel.Plan(ctx, dp, list(range(p.n_sources)), ppi_bucket=tiles))
+    ctx.synchronize()
+    for a, b in zip(got, ref):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.all(np.abs(a - b) <= 1e-5 * np.abs(b) + 1e-6 * np.abs(b).max())
