@@ -169,6 +169,31 @@ bool prepare_model(const celeste_model* m, ModelDev* md) {
   md->log_beta_axis = lgamma(m->e_axis[0]) + lgamma(m->e_axis[1]) - lgamma(m->e_axis[0] + m->e_axis[1]);
   md->log_beta_profile =
       lgamma(m->e_profile[0]) + lgamma(m->e_profile[1]) - lgamma(m->e_profile[0] + m->e_profile[1]);
+  ModelDev::F32& f = md->f;
+  for (int i = 0; i < 2; ++i) {
+    f.prior_r[i][0] = (float)md->prior_r[i][0];
+    f.prior_r[i][1] = (float)md->prior_r[i][1];
+    f.log_prior_r2[i] = (float)md->log_prior_r2[i];
+    for (int j = 0; j < kMaxColor; ++j) {
+      f.color_logdet[i][j] = (float)md->color_logdet[i][j];
+      f.log_color_w[i][j] = (float)md->log_color_w[i][j];
+      for (int k = 0; k < 4; ++k) {
+        f.color_mean[i][j][k] = (float)md->color_mean[i][j][k];
+        for (int l = 0; l < 4; ++l) f.color_prec[i][j][k][l] = (float)md->color_prec[i][j][k][l];
+      }
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    f.e_radius[k] = (float)md->e_radius[k];
+    f.e_profile[k] = (float)md->e_profile[k];
+    f.e_axis[k] = (float)md->e_axis[k];
+  }
+  f.log_prior_a = (float)md->log_prior_a;
+  f.log1m_prior_a = (float)md->log1m_prior_a;
+  f.logit_prior_a = (float)md->logit_prior_a;
+  f.half_log_2pi_e2 = (float)md->half_log_2pi_e2;
+  f.log_beta_axis = (float)md->log_beta_axis;
+  f.log_beta_profile = (float)md->log_beta_profile;
   return true;
 }
 

@@ -47,6 +47,13 @@ __device__ __forceinline__ real softplus(real t) {
 }
 
 constexpr int kEpiThreads = 128;   // four warps per source
+constexpr int kPairThreads = kEpiThreads - 32;   // warps 1..3: the pixel sums
+
+// Barrier among the kPairThreads threads of warps 1..3 (named barrier 1;
+// warp 0 is busy with the KL terms meanwhile).
+__device__ __forceinline__ void pair_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kPairThreads) : "memory");
+}
 
 struct EpiSmem {
   double W[kAcc];                  // one pair's sums
@@ -64,8 +71,8 @@ struct EpiSmem {
   real klj[2 * kMaxColor];         // log w_j - K_j
   real kls[8];                     // scalar KL pieces
   float T[10 * 10];                // per-image affine map w <- nu (local)
-  double Wp[2 * kAcc];             // per-half tile sums of one pair
   double red[2][kEpiThreads / 32]; // per-warp value sums
+  double vsum[2];                  // the source's value sums (relative, base)
 };
 
 // Rows a of J with J[a][c] != 0 for column c: their number and the k-th one
@@ -160,37 +167,37 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
   if (lane < 2 * kMaxColor) {
     const int i = lane / kMaxColor, j = lane % kMaxColor;
     if (j < J) {
-      const double(*P)[4] = m->color_prec[i][j];
+      const float(*P)[4] = m->f.color_prec[i][j];
       const real* cm = th + 5 + 4 * i;
       const real* lcv = th + 13 + 4 * i;
       real d[4], cv[4], pd[4];
       real tr = 0.f, quad = 0.f, slv = 0.f;
       for (int k = 0; k < 4; ++k) {
-        d[k] = cm[k] - (real)m->color_mean[i][j][k];
+        d[k] = cm[k] - m->f.color_mean[i][j][k];
         cv[k] = expf(lcv[k]);
       }
       for (int k = 0; k < 4; ++k) {
         real s = 0.f;
-        for (int l = 0; l < 4; ++l) s = fmaf((real)P[k][l], d[l], s);
+        for (int l = 0; l < 4; ++l) s = fmaf(P[k][l], d[l], s);
         pd[k] = s;
-        tr = fmaf((real)P[k][k], cv[k], tr);
+        tr = fmaf(P[k][k], cv[k], tr);
         quad = fmaf(d[k], s, quad);
         slv += lcv[k];
       }
-      const real K = 0.5f * (tr + quad - 4.f + (real)m->color_logdet[i][j] - slv);
-      S.klj[lane] = (real)m->log_color_w[i][j] - K;
+      const real K = 0.5f * (tr + quad - 4.f + m->f.color_logdet[i][j] - slv);
+      S.klj[lane] = m->f.log_color_w[i][j] - K;
       if (kMode >= 1) {
         real* o = S.klc + lane * kKlVals;
         real gk[8];
         for (int k = 0; k < 4; ++k) {
           gk[k] = pd[k];
-          gk[4 + k] = 0.5f * ((real)P[k][k] * cv[k] - 1.f);
+          gk[4 + k] = 0.5f * (P[k][k] * cv[k] - 1.f);
         }
         for (int k = 0; k < 8; ++k) o[k] = gk[k];
         int t = 8;
         for (int k = 0; k < 4; ++k)
-          for (int l = k; l < 4; ++l) o[t++] = (real)P[k][l];
-        for (int k = 0; k < 4; ++k) o[t++] = 0.5f * (real)P[k][k] * cv[k];
+          for (int l = k; l < 4; ++l) o[t++] = P[k][l];
+        for (int k = 0; k < 4; ++k) o[t++] = 0.5f * P[k][k] * cv[k];
       }
     } else {
       S.klj[lane] = -INFINITY;
@@ -242,23 +249,23 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
   __syncwarp();
   // ---- value (lane 0)
   if (lane == 0) {
-    real v = a * (-softplus(-th[0]) - (real)m->log_prior_a) +
-             (1.f - a) * (-softplus(th[0]) - (real)m->log1m_prior_a);
+    real v = a * (-softplus(-th[0]) - m->f.log_prior_a) +
+             (1.f - a) * (-softplus(th[0]) - m->f.log1m_prior_a);
     for (int i = 0; i < 2; ++i) {
-      const real R1 = (real)m->prior_r[i][0], R2 = (real)m->prior_r[i][1];
+      const real R1 = m->f.prior_r[i][0], R2 = m->f.prior_r[i][1];
       const real rm = th[1 + 2 * i], lrv = th[2 + 2 * i], rv = expf(lrv);
-      const real klr = 0.5f * ((real)m->log_prior_r2[i] - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.f);
+      const real klr = 0.5f * (m->f.log_prior_r2[i] - lrv + (rv + (rm - R1) * (rm - R1)) / R2 - 1.f);
       S.kls[2 + i] = klr + Bval[i];
       v += (i ? a : 1.f - a) * S.kls[2 + i];
     }
-    const real lr = th[24], E1 = (real)m->e_radius[0], E2 = (real)m->e_radius[1];
-    v += lr + (real)m->half_log_2pi_e2 + (lr - E1) * (lr - E1) / (2.f * E2);
+    const real lr = th[24], E1 = m->f.e_radius[0], E2 = m->f.e_radius[1];
+    v += lr + m->f.half_log_2pi_e2 + (lr - E1) * (lr - E1) / (2.f * E2);
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
-      const real b1 = (real)(which ? m->e_profile[0] : m->e_axis[0]);
-      const real b2 = (real)(which ? m->e_profile[1] : m->e_axis[1]);
+      const real b1 = (which ? m->f.e_profile[0] : m->f.e_axis[0]);
+      const real b2 = (which ? m->f.e_profile[1] : m->f.e_axis[1]);
       v += (b1 - 1.f) * softplus(-th[t]) + (b2 - 1.f) * softplus(th[t]) +
-           (real)(which ? m->log_beta_profile : m->log_beta_axis);
+           (which ? m->f.log_beta_profile : m->f.log_beta_axis);
     }
     S.kls[0] = v;
   }
@@ -274,11 +281,11 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
     const int e = kMode == 2 ? e0 : (e0 / 10) * 100 + (e0 % 10) * 10;
     const int i = e / 100, k = (e % 100) / 10, l = e % 10;
     const real* pw = S.X + i * kKlSums;       // grad(8), centred outer(36), prec(10), diag(4)
-    const real R2 = (real)m->prior_r[i][1];
+    const real R2 = m->f.prior_r[i][1];
     const real rm = th[1 + 2 * i], rv = expf(th[2 + 2 * i]);
     // gradient of K_i = KL_r + B at local k
     auto gK = [&](int kk) {
-      if (kk == 0) return (rm - (real)m->prior_r[i][0]) / R2;
+      if (kk == 0) return (rm - m->f.prior_r[i][0]) / R2;
       if (kk == 1) return 0.5f * (rv / R2 - 1.f);
       return pw[kk - 2];
     };
@@ -313,18 +320,18 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
   }
   __syncwarp();
   if (lane == 0) {
-    const real la = (real)m->logit_prior_a;
+    const real la = m->f.logit_prior_a;
     const real d2q = wq * (1.f - 2.f * a);
     S.gth[0] -= wq * (th[0] - la) + wq * (S.kls[3] - S.kls[2]);
     if (kMode == 2)
       S.Hth[0] -= wq * ((1.f - 2.f * a) * (th[0] - la) + 1.f) + d2q * (S.kls[3] - S.kls[2]);
-    const real lr = th[24], E1 = (real)m->e_radius[0], E2 = (real)m->e_radius[1];
+    const real lr = th[24], E1 = m->f.e_radius[0], E2 = m->f.e_radius[1];
     S.gth[24] -= 1.f + (lr - E1) / E2;
     if (kMode == 2) S.Hth[24 * kTheta + 24] -= 1.f / E2;
     for (int which = 0; which < 2; ++which) {
       const int t = which ? 26 : 25;
-      const real b1 = (real)(which ? m->e_profile[0] : m->e_axis[0]);
-      const real b2 = (real)(which ? m->e_profile[1] : m->e_axis[1]);
+      const real b1 = (which ? m->f.e_profile[0] : m->f.e_axis[0]);
+      const real b2 = (which ? m->f.e_profile[1] : m->f.e_axis[1]);
       const real sg = sigm(th[t]);
       S.gth[t] -= -(b1 - 1.f) * (1.f - sg) + (b2 - 1.f) * sg;
       if (kMode == 2) S.Hth[t * kTheta + t] -= (b1 + b2 - 2.f) * sg * (1.f - sg);
@@ -367,96 +374,122 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
     for (int e = tid; e < kTheta * kTheta; e += kEpiThreads) S.Hth[e] = 0.f;
   }
   __syncthreads();
-  for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
-    const PairInfo pi = v.pairs[pp];
+  // Warp 0 evaluates the KL terms, which depend on theta alone, while warps
+  // 1..3 reduce the pixel sums pair by pair (named barrier 1 among them).
+  if (wid == 0) {
+    if (!pixel_only) kl_terms<kMode>(th, model, S, lane);
+  } else {
+    const int u = tid - 32;                            // 0 .. kPairThreads - 1
+    double vr = 0.0, vb = 0.0;
     if (kMode == 0) {
-      double r = 0.0, b = 0.0;
-      for (int it = pi.item_begin + tid; it < pi.item_end; it += kEpiThreads) {
-        r += (double)v.vpartials[2 * (size_t)it];
-        b += (double)v.vpartials[2 * (size_t)it + 1];
+      // value sums of every pair's items, thread-strided, then one reduction
+      for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
+        const PairInfo pi = v.pairs[pp];
+        for (int it = pi.item_begin + u; it < pi.item_end; it += kPairThreads) {
+          vr += (double)v.vpartials[2 * (size_t)it];
+          vb += (double)v.vpartials[2 * (size_t)it + 1];
+        }
       }
-      r = warp_sum_d(r);
-      b = warp_sum_d(b);
+      vr = warp_sum_d(vr);
+      vb = warp_sum_d(vb);
       if (lane == 0) {
-        S.red[0][wid] = r;
-        S.red[1][wid] = b;
+        S.red[0][wid - 1] = vr;
+        S.red[1][wid - 1] = vb;
       }
-      __syncthreads();
-      for (int w = 0; w < kEpiThreads / 32; ++w) {
-        vrel += S.red[0][w];
-        vbase += S.red[1][w];
+      pair_sync();
+      if (u == 0) {
+        vr = S.red[0][0] + S.red[0][1] + S.red[0][2];
+        vb = S.red[1][0] + S.red[1][1] + S.red[1][2];
       }
-      __syncthreads();
-      continue;
-    }
-    // Sum of the pair's tile sums: accumulator tid % 64, tiles of one parity
-    // per half of the block, compensated (Kahan) FP32 summation whose error
-    // does not grow with the number of tiles; the halves meet in FP64.
-    {
-      const int a = tid & (kAcc - 1), half = tid >> 6;
-      float s0 = 0.f, c0 = 0.f;
-      if (kMode == 2 || a < kGradAcc) {
-        for (int it = pi.item_begin + half; it < pi.item_end; it += 2) {
-          const float y0 = v.partials[(size_t)it * kAcc + a] - c0;
-          const float t0 = s0 + y0;
-          c0 = (t0 - s0) - y0;
-          s0 = t0;
+    } else {
+      for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
+        const PairInfo pi = v.pairs[pp];
+        const celeste_image& im = v.images[pi.image];
+        if (u < kAcc) {
+          // the pair's tile sums, accumulator u: compensated (Kahan) FP32
+          // summation whose error does not grow with the number of tiles;
+          // the loads are independent of the chain, so they run ahead
+          float s0 = 0.f, c0 = 0.f;
+          if (kMode == 2 || u < kGradAcc) {
+#pragma unroll 4
+            for (int it = pi.item_begin; it < pi.item_end; ++it) {
+              const float y0 = v.partials[(size_t)it * kAcc + u] - c0;
+              const float t0 = s0 + y0;
+              c0 = (t0 - s0) - y0;
+              s0 = t0;
+            }
+          }
+          S.W[u] = (double)s0 - (double)c0;
+        } else {
+          // local affine map, FP32: w_k = sum_a T[k][a] nu_a
+          const float cal = (float)im.calib;
+          const float A0 = (float)im.wcs_A[0], A1 = (float)im.wcs_A[1];
+          const float A2 = (float)im.wcs_A[2], A3 = (float)im.wcs_A[3];
+          for (int e = u - kAcc; e < 100; e += kPairThreads - kAcc) {
+            float t = 0.f;
+            switch (e) {
+              case 0: case 11: t = cal; break;
+              case 22: case 33: t = cal * cal; break;
+              case 44: t = A0; break;
+              case 45: t = A1; break;
+              case 54: t = A2; break;
+              case 55: t = A3; break;
+              case 66: t = A0 * A0; break;
+              case 67: t = 2.f * A0 * A1; break;
+              case 68: t = A1 * A1; break;
+              case 76: t = A0 * A2; break;
+              case 77: t = A0 * A3 + A1 * A2; break;
+              case 78: t = A1 * A3; break;
+              case 86: t = A2 * A2; break;
+              case 87: t = 2.f * A2 * A3; break;
+              case 88: t = A3 * A3; break;
+              case 99: t = 1.f; break;
+              default: break;
+            }
+            S.T[e] = t;
+          }
         }
-      }
-      S.Wp[half * kAcc + a] = (double)s0 - (double)c0;
-    }
-    if (tid < 100) S.T[tid] = 0.f;
-    __syncthreads();
-    const celeste_image& im = v.images[pi.image];
-    if (tid < kAcc) S.W[tid] = S.Wp[tid] + S.Wp[kAcc + tid];
-    if (tid == kAcc) {
-      // local affine map, FP32: w_k = sum_a T[k][a] nu_a
-      const float cal = (float)im.calib;
-      const float A0 = (float)im.wcs_A[0], A1 = (float)im.wcs_A[1];
-      const float A2 = (float)im.wcs_A[2], A3 = (float)im.wcs_A[3];
-      S.T[0] = cal;
-      S.T[11] = cal;
-      S.T[22] = cal * cal;
-      S.T[33] = cal * cal;
-      S.T[44] = A0; S.T[45] = A1; S.T[54] = A2; S.T[55] = A3;
-      S.T[66] = A0 * A0; S.T[67] = 2.f * A0 * A1; S.T[68] = A1 * A1;
-      S.T[76] = A0 * A2; S.T[77] = A0 * A3 + A1 * A2; S.T[78] = A1 * A3;
-      S.T[86] = A2 * A2; S.T[87] = 2.f * A2 * A3; S.T[88] = A3 * A3;
-      S.T[99] = 1.f;
-    }
-    __syncthreads();
-    const int b = im.band;
-    auto nu_of = [b](int a) { return a < 4 ? 4 * b + a : 16 + a; };   // 4..9 -> 20..25
-    auto lo = [](int a) { return a < 4 ? a : (a < 6 ? 4 : (a < 9 ? 6 : 9)); };
-    auto hi = [](int a) { return a < 4 ? a + 1 : (a < 6 ? 6 : (a < 9 ? 9 : 10)); };
-    if (tid < 10) {
-      float gl = 0.f;
-      for (int k = lo(tid); k < hi(tid); ++k) gl += S.T[k * 10 + tid] * (float)S.W[2 + k];
-      S.gnu[nu_of(tid)] += gl;
-    } else if (kMode == 2 && tid >= 32 && tid < 32 + 55) {
-      const int e = tid - 32;
-      int a = 0, rem = e;
-      while (rem >= 10 - a) { rem -= 10 - a; ++a; }
-      const int c = a + rem;
-      float val = 0.f;
-      for (int k = lo(a); k < hi(a); ++k)
-        for (int l = lo(c); l < hi(c); ++l) {
-          const int kk = k < l ? k : l, ll = k < l ? l : k;
-          const bool zero = (kk == 2 || kk == 3) && (ll == 2 || ll == 3);
-          const float hwv = zero ? 0.f : (float)S.W[hidx(kk, ll)];
-          val = fmaf(S.T[k * 10 + a] * S.T[l * 10 + c], hwv, val);
+        pair_sync();
+        const int b = im.band;
+        auto nu_of = [b](int a) { return a < 4 ? 4 * b + a : 16 + a; };   // 4..9 -> 20..25
+        auto lo = [](int a) { return a < 4 ? a : (a < 6 ? 4 : (a < 9 ? 6 : 9)); };
+        auto hi = [](int a) { return a < 4 ? a + 1 : (a < 6 ? 6 : (a < 9 ? 9 : 10)); };
+        if (u < 10) {
+          float gl = 0.f;
+          for (int k = lo(u); k < hi(u); ++k) gl += S.T[k * 10 + u] * (float)S.W[2 + k];
+          S.gnu[nu_of(u)] += gl;
+        } else if (kMode == 2 && u >= 32 && u < 32 + 55) {
+          const int e = u - 32;
+          int a = 0, rem = e;
+          while (rem >= 10 - a) { rem -= 10 - a; ++a; }
+          const int c = a + rem;
+          float val = 0.f;
+          for (int k = lo(a); k < hi(a); ++k)
+            for (int l = lo(c); l < hi(c); ++l) {
+              const int kk = k < l ? k : l, ll = k < l ? l : k;
+              const bool zero = (kk == 2 || kk == 3) && (ll == 2 || ll == 3);
+              const float hwv = zero ? 0.f : (float)S.W[hidx(kk, ll)];
+              val = fmaf(S.T[k * 10 + a] * S.T[l * 10 + c], hwv, val);
+            }
+          const int na = nu_of(a), nc = nu_of(c);
+          S.Hnu[na * kNu + nc] += val;
+          if (na != nc) S.Hnu[nc * kNu + na] += val;
         }
-      const int na = nu_of(a), nc = nu_of(c);
-      S.Hnu[na * kNu + nc] += val;
-      if (na != nc) S.Hnu[nc * kNu + na] += val;
+        if (u == 0) {
+          vr += S.W[0];
+          vb += S.W[1];
+        }
+        pair_sync();
+      }
     }
-    vrel += S.W[0];
-    vbase += S.W[1];
-    __syncthreads();
+    if (u == 0) {
+      S.vsum[0] = vr;
+      S.vsum[1] = vb;
+    }
   }
-
-  if (wid == 0 && !pixel_only) kl_terms<kMode>(th, model, S, lane);
   __syncthreads();
+  vrel = S.vsum[0];
+  vbase = S.vsum[1];
   const double kl = pixel_only ? 0.0 : (double)S.kls[0];
   if (kMode >= 1) {
     if (wid == 0) {
@@ -509,39 +542,68 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
     }
     __syncthreads();
     if (kMode == 2) {
-      // X = H_nu J, only where J's column has support
-      for (int e = tid; e < kNu * kTheta; e += kEpiThreads) {
-        const int a = e / kTheta, c = e % kTheta;
+      // X = H_nu J where J's column has support: thread (c, g) forms rows
+      // a = g, g + 4, ... of column c, seven independent chains sharing
+      // each entry of J
+      if (tid < 4 * kTheta) {
+        const int c = tid % kTheta, g = tid / kTheta;
         const int nr = nrows(c);
-        real x = 0.f;
+        real x[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int k = 0; k < nr; ++k) {
           const int r = rowof(c, k);
-          x = fmaf(S.Hnu[a * kNu + r], S.J[r * kTheta + c], x);
+          const real jv = S.J[r * kTheta + c];
+#pragma unroll
+          for (int m = 0; m < 7; ++m) {
+            const int a = g + 4 * m;
+            if (a < kNu) x[m] = fmaf(S.Hnu[a * kNu + r], jv, x[m]);
+          }
         }
-        S.X[e] = x;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+          const int a = g + 4 * m;
+          if (a < kNu) S.X[a * kTheta + c] = x[m];
+        }
       }
       __syncthreads();
-      // Hth += J^T X (upper triangle, mirrored), plus the flux-moment
-      // second-order term sum_a kw_a (dl dl^T + diag d2l)
-      for (int e = tid; e < kTheta * kTheta; e += kEpiThreads) {
-        const int c = e / kTheta, d = e % kTheta;
-        if (d < c) continue;
+      // Hth += J^T X over d >= c (mirrored), plus the flux-moment
+      // second-order term sum_a kw_a (dl dl^T + diag d2l): thread (c, g)
+      // takes d = c + g, c + g + 4, ...
+      if (tid < 4 * kTheta) {
+        const int c = tid % kTheta, g = tid / kTheta;
         const int nr = nrows(c);
-        real x = 0.f;
+        real x[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int k = 0; k < nr; ++k) {
           const int r = rowof(c, k);
-          x = fmaf(S.J[r * kTheta + c], S.X[r * kTheta + d], x);
+          const real jv = S.J[r * kTheta + c];
+#pragma unroll
+          for (int m = 0; m < 7; ++m) {
+            const int d = c + g + 4 * m;
+            if (d < kTheta) x[m] = fmaf(jv, S.X[r * kTheta + d], x[m]);
+          }
         }
-        if (c <= 20 && d <= 20) {
+        if (c <= 20) {
           for (int k = 0; k < nr; ++k) {
             const int a = rowof(c, k);
             if (a >= 20) break;
-            x = fmaf(S.kw[a] * S.DL[a * kTheta + c], S.DL[a * kTheta + d], x);
-            if (c == d) x = fmaf(S.kw[a], S.D2L[a * kTheta + c], x);
+            const real kd = S.kw[a] * S.DL[a * kTheta + c];
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+              const int d = c + g + 4 * m;
+              if (d <= 20) {
+                x[m] = fmaf(kd, S.DL[a * kTheta + d], x[m]);
+                if (d == c) x[m] = fmaf(S.kw[a], S.D2L[a * kTheta + c], x[m]);
+              }
+            }
           }
         }
-        S.Hth[c * kTheta + d] += x;
-        if (d != c) S.Hth[d * kTheta + c] += x;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+          const int d = c + g + 4 * m;
+          if (d < kTheta) {
+            S.Hth[c * kTheta + d] += x[m];
+            if (d != c) S.Hth[d * kTheta + c] += x[m];
+          }
+        }
       }
       __syncthreads();
     }

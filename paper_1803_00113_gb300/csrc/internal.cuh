@@ -81,6 +81,17 @@ struct ModelDev {
   double log_prior_r2[2];
   double half_log_2pi_e2;          // 0.5 log(2 pi E_radius,2)
   double log_beta_axis, log_beta_profile;
+  // FP32 copies of what the KL terms of the epilogue read (that arithmetic
+  // is FP32; the host rounds each to nearest, as a device conversion would)
+  struct F32 {
+    float prior_r[2][2];
+    float color_mean[2][kMaxColor][4];
+    float color_prec[2][kMaxColor][4][4];
+    float color_logdet[2][kMaxColor], log_color_w[2][kMaxColor];
+    float e_radius[2], e_profile[2], e_axis[2];
+    float log_prior_a, log1m_prior_a, logit_prior_a, log_prior_r2[2], half_log_2pi_e2;
+    float log_beta_axis, log_beta_profile;
+  } f;
 };
 
 // Validates *m and fills *md (colour precisions, log-determinants and the KL
