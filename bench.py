@@ -239,6 +239,17 @@ def cpu_baseline(problem, seconds, order=None):
                       f"{problem.n_sources} sources ({visits} visits, {t_total:.1f} s)"}
 
 
+def parse_tiles(text):
+    """--tiles: four comma-separated non-negative pixels-per-item counts."""
+    try:
+        tiles = [int(t) for t in text.split(",")]
+    except ValueError:
+        tiles = []
+    if len(tiles) != 4 or any(t < 0 for t in tiles):
+        raise SystemExit("--tiles wants four non-negative integers, e.g. 128,256,0,0")
+    return tiles
+
+
 def derivs_source_hash(path):
     """Hash of the derivative kernel's source and build flags: pixel.cu up to
     the next kernel (its device helpers and derivs_kernel itself)."""
@@ -289,9 +300,7 @@ def run_ours(args):
         classes = cel.color_classes(problem)
         tiles = None
         if args.tiles:
-            tiles = [int(t) for t in args.tiles.split(",")]
-            if len(tiles) != 4 or any(t < 0 for t in tiles):
-                raise SystemExit("--tiles wants four non-negative integers")
+            tiles = parse_tiles(args.tiles)
         elif not args.no_autotune:
             from paper_1803_00113_gb300.autotune import autotune
             tiles, tune_report = autotune(ctx, dp, range(problem.n_sources), reps=2,

@@ -48,3 +48,11 @@ def test_reference_arm_line(capsys):
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+
+
+def test_parse_tiles():
+    import bench
+    assert bench.parse_tiles("128,256,0,0") == [128, 256, 0, 0]
+    for bad in ("128,256,0", "a,b,c,d", "1,2,3,-4", ""):
+        with pytest.raises(SystemExit):
+            bench.parse_tiles(bad)
