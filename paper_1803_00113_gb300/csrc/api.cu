@@ -170,6 +170,10 @@ bool prepare_model(const celeste_model* m, ModelDev* md) {
   md->log_beta_profile =
       lgamma(m->e_profile[0]) + lgamma(m->e_profile[1]) - lgamma(m->e_profile[0] + m->e_profile[1]);
   ModelDev::F32& f = md->f;
+  for (int j = 0; j < kMaxProf; ++j) {
+    f.tau_exp[j] = (float)md->tau_exp[j];
+    f.tau_dev[j] = (float)md->tau_dev[j];
+  }
   for (int i = 0; i < 2; ++i) {
     f.prior_r[i][0] = (float)md->prior_r[i][0];
     f.prior_r[i][1] = (float)md->prior_r[i][1];

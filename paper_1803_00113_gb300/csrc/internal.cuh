@@ -84,6 +84,7 @@ struct ModelDev {
   // FP32 copies of what the KL terms of the epilogue read (that arithmetic
   // is FP32; the host rounds each to nearest, as a device conversion would)
   struct F32 {
+    float tau_exp[kMaxProf], tau_dev[kMaxProf];
     float prior_r[2][2];
     float color_mean[2][kMaxColor][4];
     float color_prec[2][kMaxColor][4][4];

@@ -24,11 +24,21 @@ __device__ __forceinline__ float sigmoid_f(float t) {
 
 // One warp per pair; lanes over Gaussian components.  Only the patch-local
 // centre needs FP64 (reference-frame positions reach ~2000 px); everything
-// else is FP32, which keeps the records exact to ~1e-7 relative.
-__global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int first_pair,
-                             int n_pairs, int use_trial) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// else is FP32, which keeps the records exact to ~1e-7 relative.  On this
+// GPU the FP64 pipe also carries the double -> float conversions, at about
+// one warp instruction per 64 cycles of an SM sub-partition, so each warp
+// converts its theta row and its image's PSF, WCS and calibration with one
+// instruction each (a value per lane) and shares them through shared memory.
+constexpr int kSetupWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSetupWarps) setup_kernel(PlanView v,
+                                                                  const ModelDev* __restrict__ model,
+                                                                  int first_pair, int n_pairs,
+                                                                  int use_trial) {
+  __shared__ float s_th[kSetupWarps][32];    // theta, FP32
+  __shared__ float s_im[kSetupWarps][32];    // PSF [k][6], then wcs_A [4], calib
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * kSetupWarps + wib;
   if (warp >= n_pairs) return;
   const int p = first_pair + warp;
   const PairInfo pi = v.pairs[p];
@@ -36,6 +46,20 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
   const double* th = (use_trial && pi.slot >= 0) ? v.theta_trial + (size_t)pi.slot * kTheta
                                                  : v.theta + (size_t)pi.source * kTheta;
   float* rec = v.records + (size_t)p * kRecF;
+  constexpr int kPsfV = 6 * kPsf;                // PSF values: weight, mean (2), covariance (3)
+  static_assert(kTheta <= 32 && kPsfV + 5 <= 32, "one value per lane");
+  {
+    float* thf = s_th[wib];
+    float* imf = s_im[wib];
+    thf[lane] = (float)th[lane < kTheta ? lane : 0];
+    const double* src = lane < kPsfV ? &im.psf[0][0] + lane
+                                     : (lane < kPsfV + 4 ? im.wcs_A + (lane - kPsfV) : &im.calib);
+    imf[lane] = (float)*src;
+  }
+  __syncwarp();
+  const float* thf = s_th[wib];
+  const float* psf = s_im[wib];                  // psf[6 k + c]
+  const float* wcs = s_im[wib] + kPsfV;          // A0, A1, A2, A3, calib
 
   // centre in the patch's local pixel frame (FP64, then FP32)
   const double ux = th[21], uy = th[22];
@@ -43,16 +67,16 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
   const float muy = (float)(im.wcs_A[2] * ux + im.wcs_A[3] * uy + im.wcs_t[1] - (double)pi.y0);
   // Sigma_s = R^T diag(d1, d2) R, R = [[c, -s], [s, c]]  (Sec. 2.1.3)
   float s, c;
-  sincosf((float)th[23], &s, &c);
-  const float rad2 = expf(2.f * (float)th[24]);
-  const float axis = sigmoid_f((float)th[25]);
+  sincosf(thf[23], &s, &c);
+  const float rad2 = expf(2.f * thf[24]);
+  const float axis = sigmoid_f(thf[25]);
   const float d1 = rad2, d2 = axis * axis * rad2;
   const float S11 = c * c * d1 + s * s * d2;
   const float S12 = c * s * (d2 - d1);
   const float S22 = s * s * d1 + c * c * d2;
   // G = A Sigma_s A^T
-  const float a11 = (float)im.wcs_A[0], a12 = (float)im.wcs_A[1];
-  const float a21 = (float)im.wcs_A[2], a22 = (float)im.wcs_A[3];
+  const float a11 = wcs[0], a12 = wcs[1];
+  const float a21 = wcs[2], a22 = wcs[3];
   const float t11 = a11 * S11 + a12 * S12, t12 = a11 * S12 + a12 * S22;
   const float t21 = a21 * S11 + a22 * S12, t22 = a21 * S12 + a22 * S22;
   const float g11 = t11 * a11 + t12 * a12;
@@ -68,27 +92,28 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
     if (ci < kPsf) {
       k = ci;
       tau = 0.f;
-      weight = (float)im.psf[k][0];
+      weight = psf[6 * k];
     } else {
       const int r = ci - kPsf;
       k = r / (ne + nd);
       const int j = r % (ne + nd);
+      // the weight product stays FP64 (one rounding), as the oracle's
       if (j < ne) {
-        tau = (float)model->tau_exp[j];
+        tau = model->f.tau_exp[j];
         weight = (float)(im.psf[k][0] * model->alpha_exp[j]);
       } else {
-        tau = (float)model->tau_dev[j - ne];
+        tau = model->f.tau_dev[j - ne];
         weight = (float)(im.psf[k][0] * model->alpha_dev[j - ne]);
       }
     }
-    const float cxx = fmaf(tau, g11, (float)im.psf[k][3]);
-    const float cxy = fmaf(tau, g12, (float)im.psf[k][4]);
-    const float cyy = fmaf(tau, g22, (float)im.psf[k][5]);
+    const float cxx = fmaf(tau, g11, psf[6 * k + 3]);
+    const float cxy = fmaf(tau, g12, psf[6 * k + 4]);
+    const float cyy = fmaf(tau, g22, psf[6 * k + 5]);
     const float det = cxx * cyy - cxy * cxy;
     const float rdet = 1.f / det;
     float* e = rec + kHdr + ci * kCompF;
-    e[C_MX] = mux + (float)im.psf[k][1];
-    e[C_MY] = muy + (float)im.psf[k][2];
+    e[C_MX] = mux + psf[6 * k + 1];
+    e[C_MY] = muy + psf[6 * k + 2];
     e[C_P11] = cyy * rdet;
     e[C_P12] = -cxy * rdet;
     e[C_P22] = cxx * rdet;
@@ -102,18 +127,18 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
     const int b = im.band;
     float kk[2], ev[2];
     for (int i = 0; i < 2; ++i) {
-      float m = (float)th[1 + 2 * i];
-      float var = expf((float)th[2 + 2 * i]);
+      float m = thf[1 + 2 * i];
+      float var = expf(thf[2 + 2 * i]);
       for (int q = 0; q < 4; ++q) {
         const float sel = (float)kSel[b][q];
-        m += sel * (float)th[5 + 4 * i + q];
-        var += sel * sel * expf((float)th[13 + 4 * i + q]);
+        m += sel * thf[5 + 4 * i + q];
+        var += sel * sel * expf(thf[13 + 4 * i + q]);
       }
-      kk[i] = (float)im.calib * expf(m + 0.5f * var);   // calib E[l_b | a=i]
+      kk[i] = wcs[4] * expf(m + 0.5f * var);          // calib E[l_b | a=i]
       ev[i] = expm1f(var);                              // E[l^2] / E[l]^2 - 1
     }
-    const float q1 = sigmoid_f((float)th[0]);
-    const float q0 = sigmoid_f(-(float)th[0]);
+    const float q1 = sigmoid_f(thf[0]);
+    const float q0 = sigmoid_f(-thf[0]);
     rec[H_CE0] = q0 * kk[0];
     rec[H_CE1] = q1 * kk[1];
     rec[H_CM0] = q0 * kk[0] * kk[0] * (1.f + ev[0]);
@@ -124,8 +149,8 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
     rec[H_EV1] = ev[1];
     rec[H_Q0] = q0;
     rec[H_Q1] = q1;
-    rec[H_RHO] = sigmoid_f((float)th[26]);
-    rec[H_RHO1] = sigmoid_f(-(float)th[26]);
+    rec[H_RHO] = sigmoid_f(thf[26]);
+    rec[H_RHO1] = sigmoid_f(-thf[26]);
     rec[12] = rec[13] = rec[14] = rec[15] = 0.f;
   }
 }
@@ -133,9 +158,9 @@ __global__ void setup_kernel(PlanView v, const ModelDev* __restrict__ model, int
 cudaError_t launch_setup(const Launch& L, const PlanView& v, const ModelDev* model,
                          int first_pair, int n_pairs, bool use_trial) {
   if (n_pairs <= 0) return cudaSuccess;
-  const int threads = 128;
-  const int blocks = (n_pairs * 32 + threads - 1) / threads;
-  setup_kernel<<<blocks, threads, 0, L.stream>>>(v, model, first_pair, n_pairs, use_trial ? 1 : 0);
+  const int blocks = (n_pairs + kSetupWarps - 1) / kSetupWarps;
+  setup_kernel<<<blocks, 32 * kSetupWarps, 0, L.stream>>>(v, model, first_pair, n_pairs,
+                                                          use_trial ? 1 : 0);
   return cudaGetLastError();
 }
 
