@@ -73,6 +73,7 @@ struct TrSmem {
   double part[4 * 32];
   double red[8];
   float df[32], ef[32], e2f[32], gf[32];
+  float hps[32], hred[8];          // block Householder: p per row, per-warp sums
   int skip[32];                    // per Householder step: column already reduced
 };
 
@@ -623,74 +624,83 @@ __device__ void first_order(TrSmem& S, int lane, double dl) {
   __syncwarp();
 }
 
-// Householder reduction of B (FP32, in S.Bf) to tridiagonal form by warp 0
-// with rows on lanes and no block barrier; the reflections are applied to g
-// as they are made.  d, e into S.dfr, S.efr; Q^T g into S.gfr.
-__device__ void householder32(TrSmem& S) {
-  const int lane = threadIdx.x & 31;
+// Householder reduction of B (FP32, in S.Bf) to tridiagonal form by all
+// four warps: thread t owns row t / 4 of the trailing block and, in it, the
+// columns c = t (mod 4); two block barriers per reflection.  Every warp
+// reduces the pivot column itself (rows on lanes, the same shuffle tree in
+// each), so all threads take the same branch.  The reflections are applied
+// to g as they are made.  d, e into S.dfr, S.efr; Q^T g into S.gfr.
+__device__ void householder_blk(TrSmem& S) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int i = tid >> 2, sub = tid & 3;
   float* Bf = S.Bf;
-  float* vs = S.ef;            // reflector, broadcast through shared memory
-  float* ws = S.e2f;           // w = p - K v
-  float gi = lane < N ? S.gfr[lane] : 0.f;
+  float gi = i < N ? S.gfr[i] : 0.f;
   for (int k = 0; k < N - 2; ++k) {
-    const bool row = lane > k && lane < N;
-    const float xv = row ? Bf[lane * N + k] : 0.f;
-    float nrm2 = xv * xv;
+    const float xl = (lane > k && lane < N) ? Bf[lane * N + k] : 0.f;
+    float nrm2 = xl * xl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
-    const float x0 = __shfl_sync(0xffffffffu, xv, k + 1);
-    if (lane == 0) S.dfr[k] = Bf[k * N + k];
+    const float x0 = Bf[(k + 1) * N + k];
+    if (tid == 0) S.dfr[k] = Bf[k * N + k];
     if (!(nrm2 - x0 * x0 > 1e-30f * fmaxf(nrm2, 1e-30f))) {
-      if (lane == 0) S.efr[k] = x0;
+      if (tid == 0) S.efr[k] = x0;
       continue;
     }
     const float alpha = -copysignf(sqrtf(nrm2), x0);
     const float bt = __fdividef(1.f, fmaf(-x0, alpha, nrm2));
-    const float v = xv - (lane == k + 1 ? alpha : 0.f);
-    if (lane == 0) S.efr[k] = alpha;
-    vs[lane] = v;
-    __syncwarp();
-    // p = bt A v over the trailing block, four partial sums
-    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    if (tid == 0) S.efr[k] = alpha;
+    const bool row = i > k && i < N;
+    // reflector v_c = B[c][k] - alpha [c == k + 1], c > k (column k is not
+    // written during this reflection)
+    auto vof = [&](int c) { return Bf[c * N + k] - (c == k + 1 ? alpha : 0.f); };
+    const float vi = row ? vof(i) : 0.f;
+    const int c0 = k + 1 + ((sub - (k + 1)) & 3);   // first c > k with c = sub (mod 4)
+    // p = bt B v over the trailing block: this thread's columns, then the row
+    float pp = 0.f;
     if (row) {
-      const float* r = Bf + lane * N;
-      int c = k + 1;
-      for (; c + 3 < N; c += 4) {
-        p0 = fmaf(r[c], vs[c], p0);
-        p1 = fmaf(r[c + 1], vs[c + 1], p1);
-        p2 = fmaf(r[c + 2], vs[c + 2], p2);
-        p3 = fmaf(r[c + 3], vs[c + 3], p3);
-      }
-      for (; c < N; ++c) p0 = fmaf(r[c], vs[c], p0);
+      const float* r = Bf + i * N;
+      for (int c = c0; c < N; c += 4) pp = fmaf(r[c], vof(c), pp);
     }
-    const float p = row ? bt * ((p0 + p1) + (p2 + p3)) : 0.f;
-    // K = v.p and v.g: two reductions with interleaved shuffle trees
-    float K = v * p, vg = v * gi;
+    pp += __shfl_xor_sync(0xffffffffu, pp, 1);
+    pp += __shfl_xor_sync(0xffffffffu, pp, 2);
+    const float p = row ? bt * pp : 0.f;
+    // K = v.p and v.g over the rows (row values on sub 0), then the warps
+    float K = sub == 0 ? vi * p : 0.f, vg = sub == 0 ? vi * gi : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o >= 4; o >>= 1) {
       K += __shfl_xor_sync(0xffffffffu, K, o);
       vg += __shfl_xor_sync(0xffffffffu, vg, o);
     }
-    const float w = fmaf(-0.5f * bt * K, v, p);
-    ws[lane] = w;
-    gi = fmaf(-bt * vg, v, gi);                   // g -= bt v (v.g)
-    __syncwarp();
-    if (row) {
-      float* r = Bf + lane * N;
-      int c = k + 1;
-#pragma unroll 4
-      for (; c < N; ++c) r[c] = fmaf(-v, ws[c], fmaf(-w, vs[c], r[c]));
+    if (lane == 0) {
+      S.hred[wid] = K;
+      S.hred[4 + wid] = vg;
     }
-    __syncwarp();
+    if (sub == 0 && row) S.hps[i] = p;
+    __syncthreads();
+    K = (S.hred[0] + S.hred[1]) + (S.hred[2] + S.hred[3]);
+    vg = (S.hred[4] + S.hred[5]) + (S.hred[6] + S.hred[7]);
+    gi = fmaf(-bt * vg, vi, gi);                  // g -= bt v (v.g)
+    // B -= v w^T + w v^T with w = p - (bt K / 2) v
+    const float hk = -0.5f * bt * K;
+    if (row) {
+      const float wi = fmaf(hk, vi, p);
+      float* r = Bf + i * N;
+      for (int c = c0; c < N; c += 4) {
+        const float vc = vof(c);
+        const float wc = fmaf(hk, vc, S.hps[c]);
+        r[c] = fmaf(-vi, wc, fmaf(-wi, vc, r[c]));
+      }
+    }
+    __syncthreads();
   }
-  if (lane == 0) {
+  if (tid == 0) {
     S.dfr[N - 2] = Bf[(N - 2) * N + N - 2];
     S.dfr[N - 1] = Bf[(N - 1) * N + N - 1];
     S.efr[N - 2] = Bf[(N - 1) * N + N - 2];
     S.efr[N - 1] = 0.f;
   }
-  if (lane < N) S.gfr[lane] = gi;
-  __syncwarp();
+  if (sub == 0 && i < N) S.gfr[i] = gi;
+  __syncthreads();
 }
 
 // Warp 0: from the FP32 tridiagonal form, lambda_min and the multiplier to
@@ -808,10 +818,8 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     S.gfr[tid] = (float)g[tid];
   }
   __syncthreads();
-  if (wid == 0) {
-    householder32(S);
-    locate32(S, Delta);
-  }
+  householder_blk(S);
+  if (wid == 0) locate32(S, Delta);
   __syncthreads();
   const double D2 = Delta * Delta;
   bool done = false;
