@@ -257,7 +257,9 @@ def derivs_source_hash(path):
     from paper_1803_00113_gb300 import build_lib
     text = open(path, "rb").read()
     cut = text.find(b"__global__ void __launch_bounds__(128) grad_kernel")
-    flags = " ".join(build_lib.FLAGS + build_lib.FILE_FLAGS.get("pixel.cu", [])).encode()
+    # include paths name this checkout's location: leave them out
+    flags = " ".join(f for f in build_lib.FLAGS + build_lib.FILE_FLAGS.get("pixel.cu", [])
+                     if not f.startswith("-I")).encode()
     return hashlib.sha256(text[:cut if cut > 0 else len(text)] + flags).hexdigest()[:16]
 
 

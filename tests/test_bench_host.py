@@ -56,3 +56,19 @@ def test_parse_tiles():
     for bad in ("128,256,0", "a,b,c,d", "1,2,3,-4", ""):
         with pytest.raises(SystemExit):
             bench.parse_tiles(bad)
+
+
+def test_derivs_traffic_file_matches_the_kernel_source(tmp_path):
+    """The committed DRAM-traffic summary is keyed to the derivative kernel's
+    source and flags, independent of where the checkout lives."""
+    import json
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = os.path.join(root, "paper_1803_00113_gb300", "csrc", "pixel.cu")
+    d = json.load(open(os.path.join(root, "profiles", "derivs_kernel_dram.json")))
+    assert d["derivs_source_sha256_16"] == bench.derivs_source_hash(src)
+    assert bench.traffic_per_launch(1000.0) == d["dram_bytes_per_visit"] * 1000.0
+    # a changed kernel source no longer matches
+    moved = tmp_path / "pixel.cu"
+    moved.write_bytes(open(src, "rb").read().replace(b"kHalfLog2e", b"kHalfLog2E"))
+    assert bench.derivs_source_hash(str(moved)) != d["derivs_source_sha256_16"]
