@@ -254,13 +254,18 @@ def derivs_source_hash(path):
     """Hash of the derivative kernel's source and build flags: pixel.cu up to
     the next kernel (its device helpers and derivs_kernel itself)."""
     import hashlib
+    import re
     from paper_1803_00113_gb300 import build_lib
     text = open(path, "rb").read()
     cut = text.find(b"__global__ void __launch_bounds__(128) grad_kernel")
+    text = text[:cut if cut > 0 else len(text)]
+    # the code only: line comments and spacing do not change the kernel
+    text = re.sub(rb"//[^\n]*", b"", text)
+    text = re.sub(rb"\s+", b" ", text)
     # include paths name this checkout's location: leave them out
     flags = " ".join(f for f in build_lib.FLAGS + build_lib.FILE_FLAGS.get("pixel.cu", [])
                      if not f.startswith("-I")).encode()
-    return hashlib.sha256(text[:cut if cut > 0 else len(text)] + flags).hexdigest()[:16]
+    return hashlib.sha256(text + flags).hexdigest()[:16]
 
 
 def traffic_per_launch(visits_per_launch):

@@ -11,7 +11,8 @@
 //   * accumulates the value, the gradient and the Hessian over the 10
 //     per-image natural coordinates w = (cE0, cE1, cM0, cM1, mu, G, rho).
 // The warp reduces its 64 sums with shuffles and writes them to the item's
-// slot; the epilogue chains them to the 27 coordinates in FP64.
+// slot; the epilogue adds a pair's items (compensated FP32, the value sums
+// in FP64) and chains them to the 27 coordinates.
 //
 // Derivatives of a Gaussian component with respect to its covariance come
 // from the heat equation (d phi / dC_ab = 1/2 d^2 phi / dmu_a dmu_b), so the

@@ -68,7 +68,10 @@ def test_derivs_traffic_file_matches_the_kernel_source(tmp_path):
     d = json.load(open(os.path.join(root, "profiles", "derivs_kernel_dram.json")))
     assert d["derivs_source_sha256_16"] == bench.derivs_source_hash(src)
     assert bench.traffic_per_launch(1000.0) == d["dram_bytes_per_visit"] * 1000.0
-    # a changed kernel source no longer matches
+    text = open(src, "rb").read()
+    # a changed kernel source no longer matches; a changed comment does
     moved = tmp_path / "pixel.cu"
-    moved.write_bytes(open(src, "rb").read().replace(b"kHalfLog2e", b"kHalfLog2E"))
+    moved.write_bytes(text.replace(b"kHalfLog2e", b"kHalfLog2E"))
     assert bench.derivs_source_hash(str(moved)) != d["derivs_source_sha256_16"]
+    moved.write_bytes(text.replace(b"// Pixel kernels:", b"// Pixel kernels, reworded:\n//"))
+    assert bench.derivs_source_hash(str(moved)) == d["derivs_source_sha256_16"]
