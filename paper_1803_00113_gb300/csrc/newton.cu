@@ -41,7 +41,6 @@ constexpr double kFtol = 1e-9;
 constexpr double kDeltaMin = 1e-8;
 
 constexpr int kTri = N * (N + 1) / 2;                        // 378 lower entries
-constexpr int kOwn = (kTri + kTrThreads - 1) / kTrThreads;   // 3 per thread
 
 struct TrSmem {
   double B[N * N];
