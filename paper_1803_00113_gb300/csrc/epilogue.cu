@@ -341,9 +341,10 @@ __device__ void kl_terms(const real* th, const ModelDev* m, EpiSmem& S, int lane
 }
 
 // kMode: 0 value, 1 value + gradient, 2 value + gradient + Hessian.  Four
-// warps per source: the tile sums, the per-image maps and the two dense
-// products (X = H_nu J, H_theta += J^T X) are spread over 128 threads; the
-// KL terms and the Jacobian rows run on warp 0.
+// warps per source: warp 0 evaluates the KL terms while warps 1..3 reduce
+// the tile sums and apply the per-image maps; then warp 0 forms the Jacobian
+// rows and the two dense products (X = H_nu J, H_theta += J^T X) are spread
+// over the block in register-blocked chains.
 template <int kMode>
 __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
                                                                const ModelDev* __restrict__ model,
