@@ -45,3 +45,20 @@ def test_colouring_is_proper_and_greedy():
         assert np.all(col[nb] != col[s])
         lower = {int(col[t]) for t in nb if t < s}
         assert int(col[s]) == min(set(range(len(lower) + 1)) - lower)
+
+
+def test_colouring_equals_the_oracle_classes():
+    """The library's host colouring and the oracle's colour classes follow the
+    same greedy rule (ascending id) and must agree exactly."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1803_00113_gb300 import celeste
+    import fields
+    from oracle import newton as ON
+    for seed in (3, 4):
+        p = fields.batched(seed=seed, n_sources=80, max_images_per_band=1, max_neighbours=8)
+        col = celeste.color_sources(p.nbr_ptr, p.nbr_idx)
+        classes = ON.overlap_classes(p)
+        assert len(classes) == int(col.max()) + 1
+        for c, members in enumerate(classes):
+            assert members == [int(s) for s in np.flatnonzero(col == c)]
