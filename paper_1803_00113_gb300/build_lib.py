@@ -2,8 +2,11 @@
 
 Each translation unit compiles in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3``; the objects link
-into ``paper_1803_00113_gb300/lib/libceleste.so``.  Rebuilds only when a
-source or header is newer than the library.
+into ``paper_1803_00113_gb300/lib/libceleste.so``.  Rebuilds unless the
+library was built here from exactly the current sources, headers, flags and
+compiler: a hash of all of them is written beside the library after each
+build and compared before reusing it (a library copied in from elsewhere,
+whatever its timestamp, has no matching hash and is rebuilt).
 """
 from __future__ import annotations
 
@@ -37,16 +40,44 @@ def _nvcc():
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "celeste.h"))
     return files
 
 
+STAMP = LIB + ".sha256"
+
+
+def _nvcc_version(nvcc):
+    try:
+        return subprocess.run([nvcc, "--version"], capture_output=True, text=True).stdout
+    except OSError:
+        return ""
+
+
+def source_hash(nvcc=None):
+    """SHA-256 over every input of the build: the sources and headers (by
+    name and content), the source list, the flags and the compiler version."""
+    import hashlib
+    import platform
+    h = hashlib.sha256()
+    for f in sorted(_inputs()):
+        h.update(os.path.basename(f).encode() + b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    flags = [f for f in FLAGS if not f.startswith("-I")]
+    h.update(repr((SOURCES, ARCH, flags, sorted(FILE_FLAGS.items()),
+                   platform.machine())).encode())
+    h.update(_nvcc_version(nvcc or _nvcc()).encode())
+    return h.hexdigest()
+
+
 def needs_build():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _inputs())
+    with open(STAMP) as f:
+        return f.read().strip() != source_hash()
 
 
 def build(force=False, verbose=False):
@@ -56,6 +87,9 @@ def build(force=False, verbose=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(OBJ_DIR, exist_ok=True)
     nvcc = _nvcc()
+    digest = source_hash(nvcc)
+    if os.path.exists(STAMP):
+        os.unlink(STAMP)
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, src.replace(".cu", ".o"))
@@ -77,6 +111,8 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

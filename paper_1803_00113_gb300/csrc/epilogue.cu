@@ -24,6 +24,7 @@
 // is on the critical path of every colour class.
 #include <math.h>
 
+#include "device_once.h"
 #include "internal.cuh"
 
 namespace celeste {
@@ -632,20 +633,20 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(PlanView v,
   }
 }
 
+// The dynamic shared memory limit of each epilogue kernel, once per device.
 template <int kMode>
-static void set_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(epilogue_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(EpiSmem));
-    done = true;
-  }
+static cudaError_t set_smem_attr() {
+  static DeviceOnce once;
+  return once.run([] {
+    return cudaFuncSetAttribute(epilogue_kernel<kMode>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EpiSmem));
+  });
 }
 
 cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* model,
                             double* elbo, double* elbo_rel, double* grad, double* hess) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<2>();
+  if (cudaError_t e = set_smem_attr<2>()) return e;
   epilogue_kernel<2><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
                                                               hess, 0);
   return cudaGetLastError();
@@ -654,7 +655,7 @@ cudaError_t launch_epilogue(const Launch& L, const PlanView& v, const ModelDev* 
 cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const ModelDev* model,
                                  double* elbo, double* elbo_rel, double* grad) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<1>();
+  if (cudaError_t e = set_smem_attr<1>()) return e;
   epilogue_kernel<1><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, grad,
                                                               nullptr, 0);
   return cudaGetLastError();
@@ -663,7 +664,7 @@ cudaError_t launch_epilogue_grad(const Launch& L, const PlanView& v, const Model
 cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
                                   double* elbo, double* elbo_rel, bool use_trial) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<0>();
+  if (cudaError_t e = set_smem_attr<0>()) return e;
   epilogue_kernel<0><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, elbo, elbo_rel, nullptr,
                                                               nullptr, use_trial ? 1 : 0);
   return cudaGetLastError();
@@ -672,7 +673,7 @@ cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const Mode
 cudaError_t launch_epilogue_loglik(const Launch& L, const PlanView& v, const ModelDev* model,
                                    double* out) {
   if (v.n == 0) return cudaSuccess;
-  set_smem_attr<0>();
+  if (cudaError_t e = set_smem_attr<0>()) return e;
   epilogue_kernel<0><<<v.n, kEpiThreads, sizeof(EpiSmem), L.stream>>>(v, model, nullptr, out,
                                                                       nullptr, nullptr, 2);
   return cudaGetLastError();
@@ -695,11 +696,12 @@ __global__ void kl_kernel(PlanView v, const ModelDev* __restrict__ model, double
 
 cudaError_t launch_kl(const Launch& L, const PlanView& v, const ModelDev* model, double* kl_out) {
   if (v.n == 0) return cudaSuccess;
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(kl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EpiSmem));
-    done = true;
-  }
+  static DeviceOnce once;
+  cudaError_t e = once.run([] {
+    return cudaFuncSetAttribute(kl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(EpiSmem));
+  });
+  if (e != cudaSuccess) return e;
   kl_kernel<<<v.n, 32, sizeof(EpiSmem), L.stream>>>(v, model, kl_out);
   return cudaGetLastError();
 }

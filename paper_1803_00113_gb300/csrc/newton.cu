@@ -29,6 +29,7 @@
 // double (up to 100) when rho > 3/4 and the step reached the boundary.
 #include <math.h>
 
+#include "device_once.h"
 #include "internal.cuh"
 
 namespace celeste {
@@ -1008,20 +1009,24 @@ __global__ void mark_active_kernel(PlanView v, const int32_t* status) {
       (st == CELESTE_ST_CONVERGED || st == CELESTE_ST_FAILED || st == CELESTE_ST_MAXITER) ? 0 : 1;
 }
 
-static bool g_attr_set = false;
-static void set_attrs() {
-  if (g_attr_set) return;
-  cudaFuncSetAttribute(tr_subproblem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(TrSmem));
-  cudaFuncSetAttribute(tr_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(TrSmem));
-  g_attr_set = true;
+// The dynamic shared memory limit of the trust-region kernels, once per device.
+static DeviceOnce g_tr_attrs;
+static cudaError_t set_attrs() {
+  return g_tr_attrs.run([] {
+    cudaError_t e = cudaFuncSetAttribute(tr_subproblem_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TrSmem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tr_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(TrSmem));
+    return e;
+  });
 }
 
 cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const double* H,
                                  const double* delta, double* p, double* pred) {
   if (n <= 0) return cudaSuccess;
-  set_attrs();
+  if (cudaError_t e = set_attrs()) return e;
   tr_subproblem_kernel<<<n, kTrThreads, sizeof(TrSmem), L.stream>>>(n, g, H, delta, p, pred);
   return cudaGetLastError();
 }
@@ -1029,7 +1034,7 @@ cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const 
 cudaError_t launch_tr_step(const Launch& L, const PlanView& v, const double* delta,
                            int32_t* status) {
   if (v.n <= 0) return cudaSuccess;
-  set_attrs();
+  if (cudaError_t e = set_attrs()) return e;
   tr_step_kernel<<<v.n, kTrThreads, sizeof(TrSmem), L.stream>>>(v, delta, status);
   return cudaGetLastError();
 }

@@ -19,6 +19,7 @@
 // kernel only needs the Hermite polynomials of orders 0..4 in y = P (p - mu).
 #include <math.h>
 
+#include "device_once.h"
 #include "internal.cuh"
 
 namespace celeste {
@@ -841,33 +842,45 @@ static size_t smem_bytes_derivs(int wpb) { return (size_t)wpb * kDerivRecF * siz
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
-// Resident blocks per SM of each persistent pixel kernel (0 until measured).
+// Resident blocks per SM of each persistent pixel kernel, per device (0
+// until measured on that device).
 enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccKinds };
-static int g_occ[kOccKinds] = {0, 0, 0, 0, 0};
+static std::atomic<int> g_occ[kMaxDevices][kOccKinds] = {};
+static DeviceOnce g_occ_once;
 
 cudaError_t init_pixel_occupancy() {
-  const size_t sm = smem_bytes(kWpb);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccDerivs], derivs_kernel,
-                                                                kWpb * 32, smem_bytes_derivs(kWpb));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccGrad], grad_kernel, kWpb * 32,
-                                                       smem_bytes_derivs(kWpb));
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccValue], value_kernel, kWpb * 32, sm);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccBackground], background_kernel,
-                                                      kWpb * 32, sm);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ[kOccRender], render_cache_kernel,
-                                                      kWpb * 32, sm);
-  return e;
+  return g_occ_once.run([] {
+    const int dev = current_device();
+    const size_t sm = smem_bytes(kWpb);
+    int occ[kOccKinds] = {0, 0, 0, 0, 0};
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccDerivs], derivs_kernel,
+                                                                  kWpb * 32, smem_bytes_derivs(kWpb));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGrad], grad_kernel, kWpb * 32,
+                                                         smem_bytes_grad(kWpb));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValue], value_kernel, kWpb * 32, sm);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccBackground], background_kernel,
+                                                        kWpb * 32, sm);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccRender], render_cache_kernel,
+                                                        kWpb * 32, sm);
+    if (e == cudaSuccess)
+      for (int k = 0; k < kOccKinds; ++k) g_occ[dev][k].store(occ[k], std::memory_order_relaxed);
+    return e;
+  });
 }
 
 // Persistent grid: SMs x (the tuning's blocks per SM, else the kernel's
-// occupancy), no more blocks than the work needs.
+// occupancy on the current device), no more blocks than the work needs.
 static int grid_for(const Launch& L, int n_items, int wpb, int occ_kind = -1) {
   int per_sm = L.blocks_per_sm;
-  if (per_sm <= 0) per_sm = occ_kind >= 0 && g_occ[occ_kind] > 0 ? g_occ[occ_kind] : 3;
+  if (per_sm <= 0) {
+    const int occ =
+        occ_kind >= 0 ? g_occ[current_device()][occ_kind].load(std::memory_order_relaxed) : 0;
+    per_sm = occ > 0 ? occ : 3;
+  }
   const int blocks = L.sm_count * per_sm;
   const int needed = (n_items + wpb - 1) / wpb;
   return blocks < needed ? blocks : (needed > 0 ? needed : 1);
