@@ -448,20 +448,25 @@ int celeste_background(celeste_ctx* ctx, const celeste_plan* plan, float* bgE_ou
  * cudaMalloc may bring mid-work.  (The paper has no counterpart: this is a
  * property of the library, not of the method.)
  *
- * Computes what celeste_elbo_grad_hess computes (same kernels, same work
- * decomposition) for the n sources h_src_ids (HOST array) of *problem, with
- * no context and no plan: every intermediate lives in one file-scope device
- * array of CELESTE_NOALLOC_BYTES that each GPU loading the library holds
- * until the process exits.  It calls no cudaMalloc/cudaFree and no
- * allocating routine; model constants and the work decomposition are staged
- * from static host arrays with cudaMemcpyAsync.  Runs on the current device
- * and on cuda_stream (a cudaStream_t, or NULL).  Outputs as in
- * celeste_elbo_grad_hess; device_error (device uint32, may be NULL)
- * receives the device error word of this call.
+ * Computes what celeste_elbo_grad_hess computes for the n sources
+ * h_src_ids (HOST array) of *problem -- the same kernels, with the work
+ * decomposition of a plan made with the default tiles (256 pixels per item)
+ * and without the problem's render cache, whose backgrounds are bitwise the
+ * same as rendered ones -- with no context and no plan: every intermediate
+ * lives in one file-scope device array of CELESTE_NOALLOC_BYTES that each
+ * GPU loading the library holds until the process exits.  It calls no
+ * cudaMalloc/cudaFree and no allocating routine; model constants and the
+ * work decomposition are staged from static host arrays with
+ * cudaMemcpyAsync.  Runs on the current device and on cuda_stream (a
+ * cudaStream_t, or NULL).  Outputs as in celeste_elbo_grad_hess;
+ * device_error (device uint32, may be NULL) receives the device error word
+ * of this call.  Returns CELESTE_EINVAL when cuda_stream is being captured
+ * (the staging arrays are rewritten by every call).
  *
  * The first call on a device, with that device current, looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Limits: at most CELESTE_NOALLOC_MAX_SOURCES
+ * array's device address (cudaGetSymbolAddress) and the kernels'
+ * occupancy; make that first call before any stream capture on that
+ * device.  Limits: at most CELESTE_NOALLOC_MAX_SOURCES
  * sources, 4096 (source, image) patches including neighbours' patches,
  * 32768 pixel tiles of 256 pixels, and everything within the byte size;
  * larger requests return CELESTE_ETOOLARGE before any work is queued.

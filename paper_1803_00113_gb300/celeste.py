@@ -18,6 +18,8 @@ from . import build_lib
 
 N_THETA = 27
 ST_ACCEPTED, ST_REJECTED, ST_CONVERGED, ST_MAXITER, ST_FAILED = 0, 1, 2, 3, -1
+# device error word bits (celeste_synchronize, device_error outputs)
+DERR_PATCH, DERR_SKY, DERR_NONFINITE, DERR_TIMEOUT = 0x1, 0x2, 0x4, 0x8
 
 IMAGE_DTYPE = np.dtype([
     ("pix_offset", "<i8"), ("sky_offset", "<i8"),

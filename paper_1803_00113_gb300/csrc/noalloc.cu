@@ -11,11 +11,13 @@
 // file-scope device array of fixed size, CELESTE_NOALLOC_BYTES.  Each GPU
 // that loads the library holds that array until the process exits.
 //
-// The kernels are the ones celeste_elbo_grad_hess runs, with the same work
-// decomposition, so the outputs agree with it.
+// The kernels are the ones celeste_elbo_grad_hess runs, with the work
+// decomposition of a plan made with the default tiles (256 pixels per item)
+// and no render cache, so the outputs agree with it.
 #include <math.h>
 #include <string.h>
 
+#include "device_once.h"
 #include "internal.cuh"
 
 using namespace celeste;
@@ -33,13 +35,12 @@ constexpr int kMaxItems = 32768;
 constexpr int kMaxNbrRefs = 16384;
 constexpr int kPixelsPerItem = 256;   // the default tile of celeste_plan_create
 
-constexpr int kMaxDevices = 64;
 struct DeviceSetup {
-  bool ready;
   unsigned char* scratch;   // device address of g_noalloc_scratch on this device
   int sm_count;
 };
 static DeviceSetup g_setup[kMaxDevices];
+static DeviceOnce g_setup_once;
 
 // host staging of one call
 static PairInfo h_pairs[kMaxPairs];
@@ -49,24 +50,54 @@ static int32_t h_slot[kMaxSlots + 1];
 static int32_t h_ids[kMaxSlots];
 static ModelDev h_model;
 
+// Neighbour pairs already laid out in this call, keyed by (source, patch):
+// open addressing over twice kMaxPairs slots; a slot belongs to this call
+// when its stamp equals the call's.
+constexpr int kPairSlots = 2 * kMaxPairs;
+static uint64_t h_key[kPairSlots];
+static uint32_t h_stamp[kPairSlots];
+static int32_t h_index[kPairSlots];
+static uint32_t g_call = 0;
+
+int* pair_slot(int32_t source, int32_t patch, bool* found) {
+  const uint64_t key = ((uint64_t)(uint32_t)source << 32) | (uint32_t)patch;
+  uint64_t h = key * 0x9E3779B97F4A7C15ull;
+  for (uint32_t i = (uint32_t)(h >> 40) % kPairSlots;; i = (i + 1) % kPairSlots) {
+    if (h_stamp[i] != g_call) {
+      h_stamp[i] = g_call;
+      h_key[i] = key;
+      *found = false;
+      return &h_index[i];
+    }
+    if (h_key[i] == key) {
+      *found = true;
+      return &h_index[i];
+    }
+  }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Once per device, with that device current: the device address of the
-// scratch array (the array's name in host code is only a stand-in).
+// scratch array (the array's name in host code is only a stand-in), the SM
+// count and the pixel kernels' occupancy.
 int device_setup(int dev, DeviceSetup** out) {
   if (dev < 0 || dev >= kMaxDevices) return CELESTE_EINVAL;
   DeviceSetup& d = g_setup[dev];
-  if (!d.ready) {
+  const cudaError_t e = g_setup_once.run([&] {
     void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr)
-      return CELESTE_ECUDA;
+    cudaError_t r = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (r == cudaSuccess && ptr == nullptr) r = cudaErrorInvalidSymbol;
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return CELESTE_ECUDA;
-    d.scratch = static_cast<unsigned char*>(ptr);
-    d.sm_count = sms;
-    d.ready = true;
-  }
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r == cudaSuccess) r = init_pixel_occupancy();
+    if (r == cudaSuccess) {
+      d.scratch = static_cast<unsigned char*>(ptr);
+      d.sm_count = sms;
+    }
+    return r;
+  });
+  if (e != cudaSuccess) return CELESTE_ECUDA;
   *out = &d;
   return CELESTE_OK;
 }
@@ -90,6 +121,12 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
   int rc = device_setup(dev, &ds);
   if (rc) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // The work decomposition is staged from host arrays that the next call
+  // overwrites, so work recorded for later replay would upload whatever the
+  // last call left there: refuse a stream that is being captured.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return CELESTE_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return CELESTE_EINVAL;
 
   // ---- work decomposition (same rules and order as celeste_plan_create)
   for (int j = 0; j < n; ++j) {
@@ -141,6 +178,10 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
     h_slot[j + 1] = np;
   }
   const int n_own = np;
+  if (++g_call == 0) {              // stamps wrapped: forget every slot
+    memset(h_stamp, 0, sizeof(h_stamp));
+    g_call = 1;
+  }
   for (int pp = 0; pp < n_own; ++pp) {
     const PairInfo pi = h_pairs[pp];
     h_pairs[pp].nbr_begin = nn;
@@ -154,12 +195,9 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
         if (P.x0 >= pi.x0 + pi.w || pi.x0 >= P.x0 + P.w || P.y0 >= pi.y0 + pi.h ||
             pi.y0 >= P.y0 + P.h)
           continue;
-        int idx = -1;
-        for (int e = n_own; e < np; ++e)
-          if (h_pairs[e].source == t && h_pairs[e].patch == q) {
-            idx = e;
-            break;
-          }
+        bool found = false;
+        int* slot = pair_slot(t, q, &found);
+        int idx = found ? *slot : -1;
         if (idx < 0) {
           if (np >= kMaxPairs) return CELESTE_ETOOLARGE;
           const celeste_image& im = pr->h_images[P.image];
@@ -178,6 +216,7 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
           qn.band = im.band;
           qn.bg_base = -1;
           idx = np;
+          *slot = idx;
           h_pairs[np++] = qn;
         }
         if (nn >= kMaxNbrRefs) return CELESTE_ETOOLARGE;
@@ -255,7 +294,7 @@ extern "C" int celeste_elbo_grad_hess_noalloc(const celeste_model* model,
   L.stream = stream;
   L.sm_count = ds->sm_count;
   L.warps_per_block = 4;
-  L.blocks_per_sm = 3;
+  L.blocks_per_sm = 0;            // each kernel's measured occupancy
   L.pixels_per_item = kPixelsPerItem;
   L.n_exp = model->n_exp;
   L.n_dev = model->n_dev;
