@@ -55,8 +55,17 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["field", "batched", "serving", "first-order", "mcmc"],
-                    default="field")
+    ap.add_argument("--workload", choices=["batched", "field", "serving", "first-order", "mcmc"],
+                    default="batched")
+    ap.add_argument("--no-field", action="store_true",
+                    help="batched: skip the single-field run reported beside the headline")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving run reported beside the headline")
+    ap.add_argument("--derivs-reps", type=int, default=0,
+                    help="derivs-only: time the derivative kernel over this many further calls")
+    ap.add_argument("--derivs-only", action="store_true",
+                    help="profiling case: plan the first colour class of a batched problem of "
+                         "--sources sources (default 2000) and evaluate it twice")
     ap.add_argument("--mcmc-sources", type=int, default=16,
                     help="mcmc: sources of the field sampled (the brightest)")
     ap.add_argument("--rates", default="50,200,500,1000,2000",
@@ -220,23 +229,34 @@ class ClockSampler:
 # the CPU baseline: the oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 
-def cpu_baseline(problem, seconds, order=None):
+def cpu_baseline(problem, seconds, order=None, threads=None):
+    """The oracle's ELBO, gradient and Hessian of sources of the workload,
+    in the given order, until `seconds` of CPU work (on `threads` threads,
+    default all the host's cores)."""
     import torch
     import oracle
     order = list(range(problem.n_sources)) if order is None else order
-    t_total, visits, used = 0.0, 0, []
-    for s in order:
-        t0 = time.perf_counter()
-        oracle.elbo_grad_hess(problem, s)
-        t_total += time.perf_counter() - t0
-        visits += problem.visits([s])
-        used.append(s)
-        if t_total >= seconds:
-            break
-    return {"value": visits / t_total, "unit": UNIT, "cores": torch.get_num_threads(),
+    prev = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        t_total, visits, used = 0.0, 0, []
+        for s in order:
+            t0 = time.perf_counter()
+            oracle.elbo_grad_hess(problem, s)
+            t_total += time.perf_counter() - t0
+            visits += problem.visits([s])
+            used.append(s)
+            if t_total >= seconds:
+                break
+        cores = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(prev)
+    return {"value": visits / t_total, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"FP64 oracle ELBO+gradient+Hessian of {len(used)} of the workload's "
-                      f"{problem.n_sources} sources ({visits} visits, {t_total:.1f} s)"}
+                      f"{problem.n_sources} sources ({visits} visits, {t_total:.1f} s)",
+            "seconds_per_source": t_total / len(used)}
 
 
 def parse_tiles(text):
@@ -286,6 +306,156 @@ def traffic_per_launch(visits_per_launch):
 # our implementation
 # ---------------------------------------------------------------------------
 
+class NewtonPass:
+    """One Newton trust-region iteration on every source of a problem, colour
+    class by colour class, as one captured CUDA graph (the bench's step).
+
+    Every step starts from the same state: theta, the trust radii, the
+    statuses and (with a render cache) the cached renders of theta, restored
+    between steps outside the timed events, as the previous iteration of a
+    fit leaves them (a fit keeps the cache current by committing the trial
+    renders of accepted steps, which the step does)."""
+
+    def __init__(self, cel, ctx, dp, classes, tiles, stream, graph=True):
+        import torch
+        self.cel, self.ctx, self.dp, self.stream = cel, ctx, dp, stream
+        self.plans = [cel.Plan(ctx, dp, c, ppi_bucket=tiles) for c in classes]
+        self.visits = sum(p.visits for p in self.plans)
+        self.delta, self.status = cel.newton_state(dp)
+        self.theta0 = dp.theta.clone()
+        self.delta0, self.status0 = self.delta.clone(), self.status.clone()
+        self.render_all()
+        self.cache0 = dp.cache.clone() if dp.cache is not None else None
+        self.graph = None
+        # the library counts the kernels it launches: one eager step's worth
+        self.reset()
+        l0 = ctx.launches()
+        self.step_eager()                         # also the warm-up before a capture
+        self.n_launch = ctx.launches() - l0
+        if graph:
+            self.reset()
+            # event timing of the derivative kernel is recorded into the graph
+            # and so runs on every replay (read with reset=False after each)
+            ctx.profile(True)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                self.step_eager()
+            stream.synchronize()
+            self.graph = g
+
+    def render_all(self):
+        if self.dp.cache is not None:
+            for p in self.plans:
+                self.cel.render_cache(p)
+
+    def reset(self):
+        self.dp.theta.copy_(self.theta0)
+        self.delta.copy_(self.delta0)
+        self.status.copy_(self.status0)
+        if self.cache0 is not None:
+            self.dp.cache.copy_(self.cache0)
+
+    def step_eager(self):
+        for p in self.plans:
+            self.cel.newton_step(p, self.delta, self.status)
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step_eager()
+
+    def launches_per_step(self):
+        return self.n_launch
+
+    def close(self):
+        for p in self.plans:
+            p.close()
+
+
+def time_steps(pas, steps, flush, timed_kinds=("derivs",)):
+    """Times `steps` steps with CUDA events on the launching stream, L2
+    flushed between steps (outside the events).  Returns per-step ms and the
+    event-timed kernels of the kinds in timed_kinds, summed over the steps."""
+    import torch
+    ctx, stream = pas.ctx, pas.stream
+    if pas.graph is None:
+        ctx.profile(True, kinds=list(timed_kinds))
+    by_kind = {k: [0.0, 0, 0] for k in pas.cel.KERNEL_KINDS}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        pas.reset()
+        flush.zero_()
+        ev[k][0].record(stream)
+        pas.step()
+        ev[k][1].record(stream)
+        stream.synchronize()
+        for kind, (ms, nl, nv) in ctx.profile_kernels(reset=pas.graph is None).items():
+            if kind in timed_kinds:
+                by_kind[kind][0] += ms
+                by_kind[kind][1] += nl
+                by_kind[kind][2] += nv
+    if pas.graph is None:
+        ctx.profile(False)
+    return [a.elapsed_time(b) for a, b in ev], by_kind
+
+
+def kernel_breakdown(pas, flush):
+    """Every kernel kind of one eager step, event-timed (kept out of the
+    timed region, where only the derivative kernel is timed)."""
+    import torch
+    pas.ctx.profile(True, kinds="all")
+    pas.reset()
+    flush.zero_()
+    pas.step_eager()
+    torch.cuda.synchronize()
+    out = {k: {"ms": ms, "launches": nl} for k, (ms, nl, _) in
+           pas.ctx.profile_kernels(reset=True).items() if nl}
+    pas.ctx.profile(False)
+    return out
+
+
+def setup_problem(cel, problem, dev, stream, args, local):
+    """Context, device problem (render cache where neighbours are dense),
+    colour classes and tiles (autotuned unless given)."""
+    ctx = cel.Context(problem.model, device=local, stream=stream)
+    # cache renders where neighbours are dense (blends); in a sparse
+    # field re-rendering the few neighbours is cheaper than the cache
+    dense = problem.nbr_ptr[-1] >= 1.5 * problem.n_sources
+    dp = cel.DeviceProblem(problem, dev, render_cache=dense and not args.no_cache)
+    classes = cel.color_classes(problem)
+    tiles = None
+    if args.tiles:
+        tiles = parse_tiles(args.tiles)
+    elif not args.no_autotune:
+        from paper_1803_00113_gb300.autotune import autotune
+        tiles, _ = autotune(ctx, dp, range(problem.n_sources), reps=2, groups=classes)
+        dp.set_theta(problem.theta)
+    return ctx, dp, classes, tiles
+
+
+def field_summary(cel, args, dev, stream, local, flush, rank):
+    """The 600-source single field (the shape of the paper's study set): a
+    short timed run of the same Newton pass, reported beside the headline."""
+    import torch
+    problem, cfg = workload("field", 0, SEED + 1 + rank)
+    with torch.cuda.stream(stream):
+        ctx, dp, classes, tiles = setup_problem(cel, problem, dev, stream, args, local)
+        pas = NewtonPass(cel, ctx, dp, classes, tiles, stream, graph=not args.no_graph)
+        for _ in range(3):
+            pas.reset()
+            pas.step()
+        step_ms, by_kind = time_steps(pas, max(args.steps, 10), flush)
+        breakdown = kernel_breakdown(pas, flush)
+        pas.close()
+    return {"workload": cfg["workload"], "visits_per_step": pas.visits,
+            "value": pas.visits / (np.mean(step_ms) / 1e3), "unit": UNIT,
+            "ms_per_step": float(np.mean(step_ms)), "colour_classes": len(classes),
+            "tiles_per_area_bucket": tiles or [256, 256, 256, 256],
+            "kernels_one_step": breakdown}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_info()
@@ -296,68 +466,20 @@ def run_ours(args):
     build_lib.build()
     from paper_1803_00113_gb300 import celeste as cel
 
+    if args.derivs_only:
+        return derivs_only_case(cel, args)
+
     problem, cfg = workload(args.workload, args.sources, SEED + 1 + rank)
     stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     with torch.cuda.stream(stream):
-        ctx = cel.Context(problem.model, device=local, stream=stream)
-        # cache renders where neighbours are dense (blends); in a sparse
-        # field re-rendering the few neighbours is cheaper than the cache
-        dense = problem.nbr_ptr[-1] >= 1.5 * problem.n_sources
-        dp = cel.DeviceProblem(problem, dev, render_cache=dense and not args.no_cache)
-        classes = cel.color_classes(problem)
-        tiles = None
-        if args.tiles:
-            tiles = parse_tiles(args.tiles)
-        elif not args.no_autotune:
-            from paper_1803_00113_gb300.autotune import autotune
-            tiles, tune_report = autotune(ctx, dp, range(problem.n_sources), reps=2,
-                                          groups=classes)
-            dp.set_theta(problem.theta)
-        plans = [cel.Plan(ctx, dp, c, ppi_bucket=tiles) for c in classes]
-        visits = sum(p.visits for p in plans)
-        theta0 = dp.theta.clone()
-        delta, status = cel.newton_state(dp)
-        delta0, status0 = delta.clone(), status.clone()
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-        def reset():
-            dp.theta.copy_(theta0)
-            delta.copy_(delta0)
-            status.copy_(status0)
-
-        def step():
-            # the cache follows theta: render every source at the reset point,
-            # then each class's step refreshes the sources it moved
-            if dp.cache is not None:
-                for p in plans:
-                    cel.render_cache(p)
-            for p in plans:
-                cel.newton_step(p, delta, status)
-
-        ctx.profile(True)
+        ctx, dp, classes, tiles = setup_problem(cel, problem, dev, stream, args, local)
+        pas = NewtonPass(cel, ctx, dp, classes, tiles, stream, graph=not args.no_graph)
+        visits = pas.visits
         for _ in range(max(args.warmup, 1)):
-            reset()
-            step()
-        ctx.synchronize()
-        ctx.profile_read(reset=True)
-        graph = None
-        if not args.no_graph:
-            ctx.profile(True)
-            reset()
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=stream):
-                step()
-            stream.synchronize()
-            for _ in range(2):
-                reset()
-                graph.replay()
-            ctx.synchronize()
-
-        def run_step():
-            if graph is not None:
-                graph.replay()
-            else:
-                step()
+            pas.reset()
+            pas.step()
+        torch.cuda.synchronize(dev)
 
         # ---- timed region: K steps, L2 flushed between steps (outside the events)
         barrier(world)
@@ -365,53 +487,25 @@ def run_ours(args):
         clocks = ClockSampler(local)
         clocks.start()
         l0 = ctx.launches()
-        by_kind = {k: [0.0, 0, 0] for k in cel.KERNEL_KINDS}
-
-        def add_kinds(d):
-            for k, (ms, nl, nv) in d.items():
-                by_kind[k][0] += ms
-                by_kind[k][1] += nl
-                by_kind[k][2] += nv
-
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for k in range(args.steps):
-            reset()
-            flush.zero_()
-            ev[k][0].record(stream)
-            run_step()
-            ev[k][1].record(stream)
-            if graph is not None:
-                stream.synchronize()
-                add_kinds(ctx.profile_kernels(reset=False))
+        step_ms, by_kind = time_steps(pas, args.steps, flush)
         torch.cuda.synchronize(dev)
-        if graph is None:
-            add_kinds(ctx.profile_kernels(reset=True))
+        clk = clocks.stop()
         kern_ms, kern_launch, kern_visits = by_kind["derivs"]
         n_launch = ctx.launches() - l0
-        if graph is not None:
+        if pas.graph is not None:
             # a replay launches the captured kernels: count them per step
-            n_launch = (ctx.launches() - l0) + args.steps * launches_per_step(plans, dp.cache is not None)
-        clk = clocks.stop()
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        ctx.synchronize()
+            n_launch += args.steps * pas.launches_per_step()
         barrier(world)
         total_s = reduce_max(sum(step_ms) / 1e3, world, dev)
         all_visits = reduce_sum(visits * args.steps, world, dev)
         value = all_visits / total_s
 
-        # ---- per-kernel breakdown of one step (eager, every kind timed; kept
-        # out of the timed region, where only the derivative kernel is timed)
-        ctx.profile(True, kinds="all")
-        reset()
-        flush.zero_()
-        step()
-        torch.cuda.synchronize(dev)
-        breakdown = {k: {"ms": ms, "launches": nl} for k, (ms, nl, _) in
-                     ctx.profile_kernels(reset=True).items() if nl}
-        ctx.profile(False)
+        breakdown = kernel_breakdown(pas, flush)
 
-        # ---- end to end through the public API, host buffers
+        # ---- end to end through the public API, host buffers: every step
+        # uploads the pixels and theta, renders the cache of the uploaded
+        # theta (when the problem keeps one), runs the Newton pass and
+        # reads theta back
         pin_pix = torch.from_numpy(problem.pixels).pin_memory()
         pin_theta = torch.from_numpy(problem.theta.copy()).pin_memory()
         out_theta = torch.empty_like(pin_theta).pin_memory()
@@ -420,14 +514,14 @@ def run_ours(args):
         barrier(world)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
         e0.record(stream)
         for k in range(args.steps):
             dp.pixels.copy_(pin_pix, non_blocking=True)
             dp.theta.copy_(pin_theta, non_blocking=True)
-            delta.copy_(delta0)
-            status.copy_(status0)
-            run_step()
+            pas.delta.copy_(pas.delta0)
+            pas.status.copy_(pas.status0)
+            pas.render_all()
+            pas.step()
             out_theta.copy_(dp.theta, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -436,22 +530,21 @@ def run_ours(args):
 
         # ---- the plain one-source-per-launch form (same kernels)
         plain = None
-        ctx.profile(False)
         if not args.no_plain and rank == 0:
             order = [int(s) for c in classes for s in c]
             if len(order) > args.plain_sample:
                 pick = np.linspace(0, len(order) - 1, args.plain_sample).round().astype(int)
                 order = [order[k] for k in pick]
             single = {s: cel.Plan(ctx, dp, [s]) for s in order}
-            reset()
+            pas.reset()
             for s in order[:20]:
-                cel.newton_step(single[s], delta, status)
+                cel.newton_step(single[s], pas.delta, pas.status)
             torch.cuda.synchronize(dev)
-            reset()
+            pas.reset()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             for s in order:
-                cel.newton_step(single[s], delta, status)
+                cel.newton_step(single[s], pas.delta, pas.status)
                 stream.synchronize()
             plain_s = time.perf_counter() - t0
             pv = problem.visits(order)
@@ -464,7 +557,7 @@ def run_ours(args):
         # ---- gradient-only pass vs gradient + Hessian (the paper's cost ratio):
         # whole calls, and the pixel kernels alone (the calls share the
         # neighbour-background kernel, which is the same work in both)
-        big = max(plans, key=lambda p: p.visits)
+        big = max(pas.plans, key=lambda p: p.visits)
         ratio = {"visits": big.visits}
         for name, fn, kind in (("grad_hess", cel.elbo_grad_hess, "derivs"),
                                ("grad_only", cel.elbo_grad, "grad")):
@@ -483,6 +576,8 @@ def run_ours(args):
             ratio[name + "_pixel_kernel_ms"] = kinds[kind][0] / max(kinds[kind][1], 1)
             ratio[name + "_epilogue_ms"] = kinds["epilogue"][0] / max(kinds["epilogue"][1], 1)
         ratio["hess_over_grad_call"] = ratio["grad_hess_call_ms"] / ratio["grad_only_call_ms"]
+        ratio["hess_over_grad_pixel_kernel"] = (ratio["grad_hess_pixel_kernel_ms"]
+                                                / ratio["grad_only_pixel_kernel_ms"])
 
         # ---- the full-field ELBO (every pixel of every image, all KLs)
         fe = cel.FieldElbo(ctx, dp)
@@ -497,8 +592,14 @@ def run_ours(args):
         field_elbo = {"ms": a.elapsed_time(b) / 5, "value": float(fe.out[0]),
                       "pixels": int(problem.pixels.size)}
         fe.close()
-        ratio["hess_over_grad_pixel_kernel"] = (ratio["grad_hess_pixel_kernel_ms"]
-                                                / ratio["grad_only_pixel_kernel_ms"])
+        pas.close()
+
+    extra_field = None
+    if args.workload == "batched" and not args.no_field:
+        extra_field = field_summary(cel, args, dev, stream, local, flush, rank)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = serving_summary(cel, args, local)
 
     # ---- roofline of the derivative pixel kernel
     props = torch.cuda.get_device_properties(dev)
@@ -517,49 +618,86 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded fields shaped like the paper's study set)",
         "config": dict(cfg, l2="flushed between steps (256 MB write outside the timed events)",
-                       graph=graph is not None, visits_per_step=visits,
+                       graph=pas.graph is not None, visits_per_step=visits,
                        colour_classes=len(classes),
                        tiles_per_area_bucket=tiles or [256, 256, 256, 256],
                        tile_tuning=("given (--tiles)" if args.tiles else
                                     "composed: the step's colour-class plans, every kernel timed"
                                     if tiles else "default 256 pixels per item"),
-                       render_cache=dp.cache is not None),
+                       render_cache=dp.cache is not None,
+                       state_between_steps="theta, trust radii, statuses and the render cache "
+                                           "of theta restored outside the timed events"),
+        "step_ms_p50": float(np.percentile(step_ms, 50)),
+        "step_ms_p99": float(np.percentile(step_ms, 99)),
         "grad_vs_hess": ratio,
         "kernels_one_step": breakdown,
         "full_field_elbo": field_elbo,
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                       "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "includes": "pixel and theta upload, render cache of the uploaded theta, the "
+                            "Newton pass, theta download"},
         "gpu_launches": int(n_launch),
+        "gpu_launches_per_step": pas.launches_per_step(),
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "kernel": "derivs_kernel",
                      "kernel_ms_per_launch": avg_ms, "visits_per_launch": per_launch_visits,
                      "flop_per_visit": FLOP_PER_VISIT,
+                     "frac_at_4200_flop_per_visit": (achieved / peak * 4200 / FLOP_PER_VISIT)
+                     if achieved else None,
                      "executed_flop_per_visit": EXECUTED_FLOP_PER_VISIT,
                      "frac_executed": (achieved / peak * EXECUTED_FLOP_PER_VISIT / FLOP_PER_VISIT)
                      if achieved else None,
                      "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
-                                   f"lanes x 2 FLOP x {sm_max:.0f} MHz"},
+                                   f"lanes x 2 FLOP x {sm_max:.0f} MHz (unit counts, maximum "
+                                   "SM clock)"},
         "plain_per_source": plain,
     }
     if plain:
         line["vs_plain"] = value / plain["value"]
+    if extra_field:
+        line["single_field"] = extra_field
+    if serving:
+        line["serving"] = serving
     if not args.no_cpu_baseline and world == 1:
         rng = np.random.default_rng(0)
-        line["cpu_baseline"] = cpu_baseline(problem, args.cpu_seconds,
-                                            list(rng.permutation(problem.n_sources)))
+        order = list(rng.permutation(problem.n_sources))
+        line["cpu_baseline"] = cpu_baseline(problem, args.cpu_seconds, order)
+        line["cpu_baseline"]["one_core"] = cpu_baseline(problem, args.cpu_seconds, order, threads=1)
     return line
 
 
-def launches_per_step(plans, cache):
-    # per plan and Newton iteration: mark, setup, background, derivatives,
-    # epilogue, trust-region step, trial setup, trial value, trial epilogue,
-    # accept; with the render cache also the setup and render of every plan
-    # at the start of the step and the commit after the accept
-    return (13 if cache else 10) * len(plans)
+def derivs_only_case(cel, args):
+    """A small case for profiler captures of single kernels: a batched
+    problem of --sources sources (default 2,000, whose pixels exceed L2),
+    its first colour class planned, elbo_grad_hess called twice (a capture
+    skips the first derivative-kernel launch and takes the second)."""
+    n = args.sources or 2000
+    p = fields.batched(seed=SEED + 3, n_sources=n)
+    ctx = cel.Context(p.model)
+    dp = cel.DeviceProblem(p)
+    tiles = parse_tiles(args.tiles) if args.tiles else None
+    plan = cel.Plan(ctx, dp, cel.color_classes(p)[0], ppi_bucket=tiles)
+    for _ in range(2):
+        cel.elbo_grad_hess(plan)
+    ctx.synchronize()
+    out = {"case": "derivs-only", "sources": n, "visits": plan.visits,
+           "pixels_mb": p.pixels.nbytes / 1e6}
+    if args.derivs_reps:
+        # event-timed derivative kernel of further calls
+        ctx.profile(True)
+        for _ in range(args.derivs_reps):
+            cel.elbo_grad_hess(plan)
+        ms, nl, nv = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        import torch
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        tf = FLOP_PER_VISIT * nv / (ms / 1e3) / 1e12
+        out.update(derivs_ms_per_launch=ms / nl, visits_per_s=nv / (ms / 1e3),
+                   frac=tf / peak, frac_at_4200_flop_per_visit=tf / peak * 4200 / FLOP_PER_VISIT)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -666,6 +804,33 @@ def _serve_run(cel, srv, pool, arrivals):
         out.append(r)
     wall = time.perf_counter() - t0
     return out, wall
+
+
+def serving_summary(cel, args, local, rates=(200.0, 2000.0), seconds=2.0):
+    """A short serving run beside the headline: region requests at Poisson
+    arrival rates of 200 and 2,000 requests/s for `seconds` each; per rate the
+    fit latency (submit -> result ready) percentiles and the throughput."""
+    reqs = [fields.region_request(SEED + 5 + k) for k in range(args.pool)]
+    pool = [cel.Server.prepare(q) for q in reqs]
+    rng = np.random.default_rng(SEED + 5)
+    srv = cel.Server(reqs[0].model, device=local, workers=args.workers,
+                     pixels_per_item=args.serve_tile)
+    t0 = time.perf_counter()
+    _serve_run(cel, srv, pool[:8], np.zeros(8))          # warm-up: graphs, buffers
+    per_rate = {}
+    for rate in rates:
+        n = max(int(rate * seconds), 20)
+        res, wall = _serve_run(cel, srv, pool, np.cumsum(rng.exponential(1.0 / rate, n)))
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        per_rate[str(int(rate))] = {
+            "requests": n, "fit_latency_ms_p50": float(np.percentile(lat, 50)),
+            "fit_latency_ms_p99": float(np.percentile(lat, 99)), "fits_per_s": n / wall,
+            "mean_batch": float(np.mean([r["batch_requests"] for r in res]))}
+    srv.close()
+    return {"workload": "region requests: 1..64 sources, 32..512 px, 5 bands, 1..4 images per "
+                        f"band, Poisson arrivals for {seconds:g} s per rate, fits of <= 5 passes "
+                        "x <= 50 Newton iterations",
+            "rates": per_rate, "seconds": time.perf_counter() - t0}
 
 
 def run_serving(args):

