@@ -857,7 +857,7 @@ cudaError_t init_pixel_occupancy() {
                                                                   kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGrad], grad_kernel, kWpb * 32,
-                                                         smem_bytes_grad(kWpb));
+                                                         smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValue], value_kernel, kWpb * 32, sm);
     if (e == cudaSuccess)
