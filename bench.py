@@ -44,7 +44,7 @@ UNIT = "visits/s"
 # one PSF component and stages pixel-independent constants, and executes
 # EXECUTED_FLOP_PER_VISIT; the roofline reports both fractions.
 FLOP_PER_VISIT = 5320
-EXECUTED_FLOP_PER_VISIT = 4771
+EXECUTED_FLOP_PER_VISIT = 4723
 FP32_LANES_PER_SM = 128
 SEED = 1803_00113
 

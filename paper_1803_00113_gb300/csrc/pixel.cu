@@ -32,7 +32,15 @@ constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 // component: mx, my, P11, P12, P22, lw, tau) in one of two layouts:
 //   value layout:  header | origins | each component {A11, A12, A22, lw}
 //   derivs layout: header | origins | star {A, lw | P, 0}
-//                                   | galaxy {A, lw | P, tau | Hermite constants}
+//                                   | per PSF component k: galaxy pairs, then singles
+// A galaxy component has 16 values {A, lw | -P11, -P12, -P22, tau |
+// -2 P12, -2 P11^2, -2 P22^2, -2 P12^2 | -4 P12, 0, 0, 0}: the signs are
+// chosen so that no formula below negates an operand.  The components of PSF
+// component k come in pairs (exponential j, de Vaucouleurs j) for
+// j < min(n_exp, n_dev), their values interleaved (exponential in the even
+// slots), so that one packed two-wide FP32 instruction (ffma2, which rounds
+// each half as fmaf does) evaluates both; the components without a partner
+// follow with their 16 values in a row.
 // A = -log2(e)/2 (P11, 2 P12, P22) are the coefficients of the exponent's
 // quadratic form: log2 phi = lw + A11 dx^2 + A12 dx dy + A22 dy^2.  Every
 // component convolved with PSF component k has that component's mean (the
@@ -43,7 +51,7 @@ constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 constexpr int kOrgF = 8;                                   // (mx, my) per k, padded
 constexpr int kValF = 4;
 constexpr int kStarF = 8;
-constexpr int kGalF = 12;
+constexpr int kGalF = 16;
 constexpr int kCompBase = kHdr + kOrgF;
 constexpr int kValRecF = kCompBase + kMaxComp * kValF;
 constexpr int kDerivRecF = kCompBase + kPsf * kStarF + kPsf * 2 * kMaxProf * kGalF;
@@ -58,7 +66,7 @@ __device__ __forceinline__ float4 quad_coeffs(float p11, float p12, float p22, f
 // then per PSF component the exponential and de Vaucouleurs components).
 template <bool kDerivs>
 __device__ __forceinline__ void stage_record(float* __restrict__ dst, const float* __restrict__ src,
-                                             int n_comp, int lane) {
+                                             int n_comp, int lane, int n_exp = 0) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
   float4* d4 = reinterpret_cast<float4*>(dst);
   if (lane < kHdr / 4) d4[lane] = s4[lane];
@@ -77,10 +85,28 @@ __device__ __forceinline__ void stage_record(float* __restrict__ dst, const floa
       o[0] = q;
       o[1] = make_float4(p11, p12, p22, 0.f);
     } else {
-      float4* o = reinterpret_cast<float4*>(dst + kCompBase + kPsf * kStarF + (ci - kPsf) * kGalF);
-      o[0] = q;
-      o[1] = make_float4(p11, p12, p22, b.z);
-      o[2] = make_float4(2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22, -2.f * p12 * p12);
+      // galaxy component: PSF component k, index j of its profile
+      const int per = (n_comp - kPsf) / kPsf;
+      const int g = ci - kPsf, k = g / per, jj = g - k * per;
+      const int ne = n_exp;
+      const int nb = ne < per - ne ? ne : per - ne;
+      const bool dev = jj >= ne;
+      const int j = dev ? jj - ne : jj;
+      const float vals[kGalF] = {q.x, q.y, q.z, q.w, -p11, -p12, -p22, b.z,
+                                 -2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22, -2.f * p12 * p12,
+                                 -4.f * p12, 0.f, 0.f, 0.f};
+      float* base = dst + kCompBase + kPsf * kStarF + k * per * kGalF;
+      if (j < nb) {
+        float* o = base + j * 2 * kGalF + (dev ? 1 : 0);
+#pragma unroll
+        for (int e = 0; e < kGalF; ++e) o[2 * e] = vals[e];
+      } else {
+        const int single = dev ? (ne - nb) + (j - nb) : j - nb;
+        float4* o = reinterpret_cast<float4*>(base + nb * 2 * kGalF + single * kGalF);
+#pragma unroll
+        for (int e = 0; e < kGalF / 4; ++e)
+          o[e] = make_float4(vals[4 * e], vals[4 * e + 1], vals[4 * e + 2], vals[4 * e + 3]);
+      }
     }
   }
 }
@@ -105,6 +131,9 @@ __device__ __forceinline__ float gauss_density(const float4 q, const Offset& o) 
 // Sums over the components of one galaxy profile (weights without rho):
 // S*: derivatives in mu; T2: tau-weighted second order (-> dG);
 // T3: tau-weighted third order (-> d mu dG); T4: tau^2 fourth order (-> dG dG).
+// The odd orders (s1*, t3*) are accumulated with the opposite sign: the
+// kernels form z = -y = (-P) (p - mu) from the staged -P, and the Hermite
+// polynomials of odd order change sign with y.
 struct GalSums {
   float s0, s1x, s1y, s2xx, s2xy, s2yy;
   float t2xx, t2xy, t2yy;
@@ -112,25 +141,25 @@ struct GalSums {
   float t4a, t4b, t4c, t4d, t4e;       // 1111, 1112, 1122, 1222, 2222
 };
 
-// One galaxy component of the derivs layout: its 12 floats are
-// {A, lw | P11, P12, P22, tau | 2 P12, -2 P11^2, -2 P22^2, -2 P12^2}.
+// One galaxy component of the derivs layout (16 staged values).
 __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, const Offset& o,
                                                GalSums& g) {
   const float4 q = *reinterpret_cast<const float4*>(c);
   const float4 pp = *reinterpret_cast<const float4*>(c + 4);
   const float4 hc = *reinterpret_cast<const float4*>(c + 8);
-  const float P11 = pp.x, P12 = pp.y, P22 = pp.z, tau = pp.w, P12x2 = hc.x;
-  const float y1 = fmaf(P11, o.dx, P12 * o.dy);
-  const float y2 = fmaf(P12, o.dx, P22 * o.dy);
+  const float m4P12 = c[12];
+  const float nP11 = pp.x, nP12 = pp.y, nP22 = pp.z, tau = pp.w, m2P12 = hc.x;
+  const float z1 = fmaf(nP11, o.dx, nP12 * o.dy);       // -y1
+  const float z2 = fmaf(nP12, o.dx, nP22 * o.dy);       // -y2
   const float phi = gauss_density(q, o);
-  const float h11 = fmaf(y1, y1, -P11);
-  const float h12 = fmaf(y1, y2, -P12);
-  const float h22 = fmaf(y2, y2, -P22);
+  const float h11 = fmaf(z1, z1, nP11);                 // y y^T - P
+  const float h12 = fmaf(z1, z2, nP12);
+  const float h22 = fmaf(z2, z2, nP22);
   const float pt = phi * tau;
   const float pt2 = pt * tau;
   g.s0 += phi;
-  g.s1x = fmaf(phi, y1, g.s1x);
-  g.s1y = fmaf(phi, y2, g.s1y);
+  g.s1x = fmaf(phi, z1, g.s1x);
+  g.s1y = fmaf(phi, z2, g.s1y);
   g.s2xx = fmaf(phi, h11, g.s2xx);
   g.s2xy = fmaf(phi, h12, g.s2xy);
   g.s2yy = fmaf(phi, h22, g.s2yy);
@@ -138,18 +167,109 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, cons
   g.t2xy = fmaf(pt, h12, g.t2xy);
   g.t2yy = fmaf(pt, h22, g.t2yy);
   // third order: y_a y_b y_c - (P_ab y_c + P_ac y_b + P_bc y_a)
-  const float a1 = fmaf(-2.f, P11, h11), a2 = fmaf(-2.f, P22, h22);
-  const float py1 = pt * y1, py2 = pt * y2;
-  g.t3a = fmaf(py1, a1, g.t3a);
-  g.t3b = fmaf(py2, h11, fmaf(-P12x2, py1, g.t3b));
-  g.t3c = fmaf(py1, h22, fmaf(-P12x2, py2, g.t3c));
-  g.t3d = fmaf(py2, a2, g.t3d);
+  const float a1 = fmaf(2.f, nP11, h11), a2 = fmaf(2.f, nP22, h22);
+  const float pz1 = pt * z1, pz2 = pt * z2;
+  g.t3a = fmaf(pz1, a1, g.t3a);
+  g.t3b = fmaf(pz2, h11, fmaf(m2P12, pz1, g.t3b));
+  g.t3c = fmaf(pz1, h22, fmaf(m2P12, pz2, g.t3c));
+  g.t3d = fmaf(pz2, a2, g.t3d);
   // fourth order, written with h = y y^T - P
-  g.t4a = fmaf(pt2, fmaf(h11, fmaf(-4.f, P11, h11), hc.y), g.t4a);
-  g.t4b = fmaf(pt2, fmaf(h12, a1, -P12x2 * (h11 + P11)), g.t4b);
-  g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, -2.f * P12x2, hc.w)), g.t4c);
-  g.t4d = fmaf(pt2, fmaf(h12, a2, -P12x2 * (h22 + P22)), g.t4d);
-  g.t4e = fmaf(pt2, fmaf(h22, fmaf(-4.f, P22, h22), hc.z), g.t4e);
+  const float y11 = z1 * z1, y22 = z2 * z2;
+  g.t4a = fmaf(pt2, fmaf(h11, fmaf(4.f, nP11, h11), hc.y), g.t4a);
+  g.t4b = fmaf(pt2, fmaf(h12, a1, m2P12 * y11), g.t4b);
+  g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, m4P12, hc.w)), g.t4c);
+  g.t4d = fmaf(pt2, fmaf(h12, a2, m2P12 * y22), g.t4d);
+  g.t4e = fmaf(pt2, fmaf(h22, fmaf(4.f, nP22, h22), hc.z), g.t4e);
+}
+
+// ---- packed pairs (exponential j, de Vaucouleurs j) ------------------------
+// ffma2 / fmul2 / fadd2 round each half exactly as fmaf / * / + do, so the
+// packed sums equal, bit for bit, the ones the scalar code forms.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// A pixel's offset products, duplicated in both halves.
+struct Offset2 {
+  float2 dx, dy, xx, xy, yy;
+};
+__device__ __forceinline__ Offset2 dup_offset(const Offset& o) {
+  return Offset2{f2(o.dx), f2(o.dy), f2(o.xx), f2(o.xy), f2(o.yy)};
+}
+
+// The sums of GalSums for both profiles: .x exponential, .y de Vaucouleurs.
+struct GalSums2 {
+  float2 s0, s1x, s1y, s2xx, s2xy, s2yy;
+  float2 t2xx, t2xy, t2yy;
+  float2 t3a, t3b, t3c, t3d;
+  float2 t4a, t4b, t4c, t4d, t4e;
+};
+
+// gal_accumulate on a staged pair (32 floats, exponential in the even slots).
+__device__ __forceinline__ void gal_accumulate2(const float* __restrict__ c, const Offset2& o,
+                                                GalSums2& g) {
+  const float4 qa = *reinterpret_cast<const float4*>(c);
+  const float4 qb = *reinterpret_cast<const float4*>(c + 4);
+  const float4 pa = *reinterpret_cast<const float4*>(c + 8);
+  const float4 pb = *reinterpret_cast<const float4*>(c + 12);
+  const float4 ha = *reinterpret_cast<const float4*>(c + 16);
+  const float4 hb = *reinterpret_cast<const float4*>(c + 20);
+  const float2 m4P12 = *reinterpret_cast<const float2*>(c + 24);
+  const float2 A11 = make_float2(qa.x, qa.y), A12 = make_float2(qa.z, qa.w);
+  const float2 A22 = make_float2(qb.x, qb.y), lw = make_float2(qb.z, qb.w);
+  const float2 nP11 = make_float2(pa.x, pa.y), nP12 = make_float2(pa.z, pa.w);
+  const float2 nP22 = make_float2(pb.x, pb.y), tau = make_float2(pb.z, pb.w);
+  const float2 m2P12 = make_float2(ha.x, ha.y), c4a = make_float2(ha.z, ha.w);
+  const float2 c4e = make_float2(hb.x, hb.y), c4c = make_float2(hb.z, hb.w);
+  const float2 two = f2(2.f), four = f2(4.f);
+  const float2 z1 = fma2(nP11, o.dx, mul2(nP12, o.dy));
+  const float2 z2 = fma2(nP12, o.dx, mul2(nP22, o.dy));
+  const float2 arg = fma2(A11, o.xx, fma2(A12, o.xy, fma2(A22, o.yy, lw)));
+  const float2 phi = make_float2(exp2f(arg.x), exp2f(arg.y));
+  const float2 h11 = fma2(z1, z1, nP11);
+  const float2 h12 = fma2(z1, z2, nP12);
+  const float2 h22 = fma2(z2, z2, nP22);
+  const float2 pt = mul2(phi, tau);
+  const float2 pt2 = mul2(pt, tau);
+  g.s0 = add2(g.s0, phi);
+  g.s1x = fma2(phi, z1, g.s1x);
+  g.s1y = fma2(phi, z2, g.s1y);
+  g.s2xx = fma2(phi, h11, g.s2xx);
+  g.s2xy = fma2(phi, h12, g.s2xy);
+  g.s2yy = fma2(phi, h22, g.s2yy);
+  g.t2xx = fma2(pt, h11, g.t2xx);
+  g.t2xy = fma2(pt, h12, g.t2xy);
+  g.t2yy = fma2(pt, h22, g.t2yy);
+  const float2 a1 = fma2(two, nP11, h11), a2 = fma2(two, nP22, h22);
+  const float2 pz1 = mul2(pt, z1), pz2 = mul2(pt, z2);
+  g.t3a = fma2(pz1, a1, g.t3a);
+  g.t3b = fma2(pz2, h11, fma2(m2P12, pz1, g.t3b));
+  g.t3c = fma2(pz1, h22, fma2(m2P12, pz2, g.t3c));
+  g.t3d = fma2(pz2, a2, g.t3d);
+  const float2 y11 = mul2(z1, z1), y22 = mul2(z2, z2);
+  g.t4a = fma2(pt2, fma2(h11, fma2(four, nP11, h11), c4a), g.t4a);
+  g.t4b = fma2(pt2, fma2(h12, a1, mul2(m2P12, y11)), g.t4b);
+  g.t4c = fma2(pt2, fma2(h11, h22, fma2(h12, m4P12, c4c)), g.t4c);
+  g.t4d = fma2(pt2, fma2(h12, a2, mul2(m2P12, y22)), g.t4d);
+  g.t4e = fma2(pt2, fma2(h22, fma2(four, nP22, h22), c4e), g.t4e);
+}
+
+// A component without a partner: gal_accumulate into half L of g.
+template <int L>
+__device__ __forceinline__ void gal_single(const float* __restrict__ c, const Offset& o,
+                                           GalSums2& g) {
+  GalSums h;
+#define GET(f) h.f = L ? g.f.y : g.f.x;
+#define PUT(f) (L ? g.f.y : g.f.x) = h.f;
+#define ALL(M) M(s0) M(s1x) M(s1y) M(s2xx) M(s2xy) M(s2yy) M(t2xx) M(t2xy) M(t2yy) \
+               M(t3a) M(t3b) M(t3c) M(t3d) M(t4a) M(t4b) M(t4c) M(t4d) M(t4e)
+  ALL(GET)
+  gal_accumulate(c, o, h);
+  ALL(PUT)
+#undef ALL
+#undef PUT
+#undef GET
 }
 
 // Galaxy (rho-mixed) and star profile densities of one pair at a pixel
@@ -188,10 +308,36 @@ __device__ __forceinline__ void own_moments(const float* __restrict__ rec, float
             fmaf(rec[H_Q1] * rec[H_EV1] * k1F, k1F, rec[H_Q0] * rec[H_Q1] * d * d));
 }
 
+// The 52 Hessian sums of a lane live in its warp's shared memory: row a
+// (the sum hidx = kGradAcc + a) of a padded [kHessAcc][33] array, this lane's
+// column.  The 33-float rows keep both the per-pixel updates (one row, all
+// lanes) and the transposed reduction (one row per lane) free of bank
+// conflicts, and the registers this frees keep more warps resident.
+constexpr int kHessAcc = kAcc - kGradAcc;   // 52
+constexpr int kHessRow = 33;
+constexpr int kAccTileF = kAcc * kHessRow;  // all 64 sums at the reduction
+
+struct HessAcc {
+  float* __restrict__ col;   // this lane's column of the warp's array
+  __device__ __forceinline__ float* at(int idx) const { return col + (idx - kGradAcc) * kHessRow; }
+  // sum += v
+  __device__ __forceinline__ void add(int idx, float v) const { *at(idx) += v; }
+  // sum = fma(a, b, sum)
+  __device__ __forceinline__ void fma(int idx, float a, float b) const {
+    float* p = at(idx);
+    *p = fmaf(a, b, *p);
+  }
+  // sum = fma(a, b, fma(c, d, sum))
+  __device__ __forceinline__ void fma2(int idx, float a, float b, float c, float d) const {
+    float* p = at(idx);
+    *p = fmaf(a, b, fmaf(c, d, *p));
+  }
+};
+
 // One pixel: render with derivatives and accumulate value, gradient, Hessian.
 __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int ne, int nd,
                                              float px, float py, float x, float2 bg,
-                                             float* __restrict__ acc) {
+                                             float* __restrict__ acc, const HessAcc& hs) {
   // ---- star: value, d mu, d mu d mu
   float F1 = 0.f, sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
 #pragma unroll
@@ -210,24 +356,30 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
     sxy = fmaf(phi, fmaf(y1, y2, -pp.y), sxy);
     syy = fmaf(phi, fmaf(y2, y2, -pp.z), syy);
   }
-  // ---- galaxy: exponential and de Vaucouleurs sums
-  GalSums ge = {}, gd = {};
+  // ---- galaxy: exponential and de Vaucouleurs sums, evaluated in pairs
+  GalSums2 g2 = {};
   const int per = ne + nd;
+  const int nb = ne < nd ? ne : nd;
   // kept rolled: three copies of this loop cost more in instruction fetch
   // than recomputing the offsets
 #pragma unroll 1
   for (int k = 0; k < kPsf; ++k) {
     const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
     const Offset o = make_offset(pixel_delta(rec, k, px, py));
-    // the two profiles' sums are independent chains: interleave them
-    const int nb = ne < nd ? ne : nd;
-    for (int j = 0; j < nb; ++j) {
-      gal_accumulate(base + j * kGalF, o, ge);
-      gal_accumulate(base + (ne + j) * kGalF, o, gd);
-    }
-    for (int j = nb; j < ne; ++j) gal_accumulate(base + j * kGalF, o, ge);
-    for (int j = nb; j < nd; ++j) gal_accumulate(base + (ne + j) * kGalF, o, gd);
+    const Offset2 o2 = dup_offset(o);
+    for (int j = 0; j < nb; ++j) gal_accumulate2(base + j * 2 * kGalF, o2, g2);
+    const float* single = base + nb * 2 * kGalF;
+    for (int j = nb; j < ne; ++j, single += kGalF) gal_single<0>(single, o, g2);
+    for (int j = nb; j < nd; ++j, single += kGalF) gal_single<1>(single, o, g2);
   }
+  GalSums ge, gd;
+#define SPLIT(f) ge.f = g2.f.x; gd.f = g2.f.y;
+#define FLIP(f) ge.f = -g2.f.x; gd.f = -g2.f.y;        // odd orders: summed with -y
+  SPLIT(s0) FLIP(s1x) FLIP(s1y) SPLIT(s2xx) SPLIT(s2xy) SPLIT(s2yy) SPLIT(t2xx) SPLIT(t2xy)
+  SPLIT(t2yy) FLIP(t3a) FLIP(t3b) FLIP(t3c) FLIP(t3d) SPLIT(t4a) SPLIT(t4b) SPLIT(t4c)
+  SPLIT(t4d) SPLIT(t4e)
+#undef FLIP
+#undef SPLIT
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
   // galaxy density and its derivatives over (mu_x, mu_y, g11, g12, g22, rho)
@@ -313,28 +465,28 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
     cg[g] = tEM * bG[g];
     u[g] = fmaf(tEE, aG[g], cg[g]);
   }
-  acc[hidx(0, 0)] = fmaf(tEE, F0s, acc[hidx(0, 0)]);
-  acc[hidx(0, 1)] = fmaf(tEE, F0 * F1, acc[hidx(0, 1)]);
-  acc[hidx(1, 1)] = fmaf(tEE, F1s, acc[hidx(1, 1)]);
-  acc[hidx(0, 2)] = fmaf(tEM * F0, F0s, acc[hidx(0, 2)]);
-  acc[hidx(0, 3)] = fmaf(tEM * F0, F1s, acc[hidx(0, 3)]);
-  acc[hidx(1, 2)] = fmaf(tEM * F1, F0s, acc[hidx(1, 2)]);
-  acc[hidx(1, 3)] = fmaf(tEM * F1, F1s, acc[hidx(1, 3)]);
+  hs.fma(hidx(0, 0), tEE, F0s);
+  hs.fma(hidx(0, 1), tEE, F0 * F1);
+  hs.fma(hidx(1, 1), tEE, F1s);
+  hs.fma(hidx(0, 2), tEM * F0, F0s);
+  hs.fma(hidx(0, 3), tEM * F0, F1s);
+  hs.fma(hidx(1, 2), tEM * F1, F0s);
+  hs.fma(hidx(1, 3), tEM * F1, F1s);
   const float tm2F0 = 2.f * tM * F0, tm2F1 = 2.f * tM * F1;
   const float eF0 = tEM * F0s, eF1 = tEM * F1s;
 #pragma unroll
   for (int g = 0; g < 6; ++g) {
-    acc[hidx(0, 4 + g)] = fmaf(F0, u[g], fmaf(tE, d0[g], acc[hidx(0, 4 + g)]));
-    acc[hidx(2, 4 + g)] = fmaf(eF0, aG[g], fmaf(tm2F0, d0[g], acc[hidx(2, 4 + g)]));
+    hs.fma2(hidx(0, 4 + g), F0, u[g], tE, d0[g]);
+    hs.fma2(hidx(2, 4 + g), eF0, aG[g], tm2F0, d0[g]);
   }
-  acc[hidx(1, 4)] = fmaf(F1, u[0], fmaf(tE, sx, acc[hidx(1, 4)]));
-  acc[hidx(1, 5)] = fmaf(F1, u[1], fmaf(tE, sy, acc[hidx(1, 5)]));
-  acc[hidx(3, 4)] = fmaf(eF1, aG[0], fmaf(tm2F1, sx, acc[hidx(3, 4)]));
-  acc[hidx(3, 5)] = fmaf(eF1, aG[1], fmaf(tm2F1, sy, acc[hidx(3, 5)]));
+  hs.fma2(hidx(1, 4), F1, u[0], tE, sx);
+  hs.fma2(hidx(1, 5), F1, u[1], tE, sy);
+  hs.fma2(hidx(3, 4), eF1, aG[0], tm2F1, sx);
+  hs.fma2(hidx(3, 5), eF1, aG[1], tm2F1, sy);
 #pragma unroll
   for (int g = 2; g < 6; ++g) {
-    acc[hidx(1, 4 + g)] = fmaf(F1, u[g], acc[hidx(1, 4 + g)]);
-    acc[hidx(3, 4 + g)] = fmaf(eF1, aG[g], acc[hidx(3, 4 + g)]);
+    hs.fma(hidx(1, 4 + g), F1, u[g]);
+    hs.fma(hidx(3, 4 + g), eF1, aG[g]);
   }
   const float D0 = fmaf(tE, cE0, tM * m0);   // dl/dF0 (direct part)
   const float D1 = fmaf(tE, cE1, tM * m1);
@@ -352,7 +504,7 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
         v = fmaf(D1, h1[g][h], v);
         v = fmaf(q1 * d1[g], d1[h], v);
       }
-      acc[hidx(4 + g, 4 + h)] += v;
+      hs.add(hidx(4 + g, 4 + h), v);
     }
   }
 }
@@ -367,17 +519,60 @@ __device__ __forceinline__ void gal_accumulate1(const float* __restrict__ c, con
                                                 GalSums1& g) {
   const float4 q = *reinterpret_cast<const float4*>(c);
   const float4 pp = *reinterpret_cast<const float4*>(c + 4);
-  const float P11 = pp.x, P12 = pp.y, P22 = pp.z;
-  const float y1 = fmaf(P11, o.dx, P12 * o.dy);
-  const float y2 = fmaf(P12, o.dx, P22 * o.dy);
+  const float nP11 = pp.x, nP12 = pp.y, nP22 = pp.z;
+  const float z1 = fmaf(nP11, o.dx, nP12 * o.dy);       // -y1
+  const float z2 = fmaf(nP12, o.dx, nP22 * o.dy);
   const float phi = gauss_density(q, o);
   const float pt = phi * pp.w;
   g.s0 += phi;
-  g.s1x = fmaf(phi, y1, g.s1x);
-  g.s1y = fmaf(phi, y2, g.s1y);
-  g.t2xx = fmaf(pt, fmaf(y1, y1, -P11), g.t2xx);
-  g.t2xy = fmaf(pt, fmaf(y1, y2, -P12), g.t2xy);
-  g.t2yy = fmaf(pt, fmaf(y2, y2, -P22), g.t2yy);
+  g.s1x = fmaf(phi, z1, g.s1x);
+  g.s1y = fmaf(phi, z2, g.s1y);
+  g.t2xx = fmaf(pt, fmaf(z1, z1, nP11), g.t2xx);
+  g.t2xy = fmaf(pt, fmaf(z1, z2, nP12), g.t2xy);
+  g.t2yy = fmaf(pt, fmaf(z2, z2, nP22), g.t2yy);
+}
+
+struct GalSums1x2 {
+  float2 s0, s1x, s1y, t2xx, t2xy, t2yy;
+};
+
+// gal_accumulate1 on a staged pair (exponential in the even slots).
+__device__ __forceinline__ void gal_accumulate1x2(const float* __restrict__ c, const Offset2& o,
+                                                  GalSums1x2& g) {
+  const float4 qa = *reinterpret_cast<const float4*>(c);
+  const float4 qb = *reinterpret_cast<const float4*>(c + 4);
+  const float4 pa = *reinterpret_cast<const float4*>(c + 8);
+  const float4 pb = *reinterpret_cast<const float4*>(c + 12);
+  const float2 A11 = make_float2(qa.x, qa.y), A12 = make_float2(qa.z, qa.w);
+  const float2 A22 = make_float2(qb.x, qb.y), lw = make_float2(qb.z, qb.w);
+  const float2 nP11 = make_float2(pa.x, pa.y), nP12 = make_float2(pa.z, pa.w);
+  const float2 nP22 = make_float2(pb.x, pb.y), tau = make_float2(pb.z, pb.w);
+  const float2 z1 = fma2(nP11, o.dx, mul2(nP12, o.dy));
+  const float2 z2 = fma2(nP12, o.dx, mul2(nP22, o.dy));
+  const float2 arg = fma2(A11, o.xx, fma2(A12, o.xy, fma2(A22, o.yy, lw)));
+  const float2 phi = make_float2(exp2f(arg.x), exp2f(arg.y));
+  const float2 pt = mul2(phi, tau);
+  g.s0 = add2(g.s0, phi);
+  g.s1x = fma2(phi, z1, g.s1x);
+  g.s1y = fma2(phi, z2, g.s1y);
+  g.t2xx = fma2(pt, fma2(z1, z1, nP11), g.t2xx);
+  g.t2xy = fma2(pt, fma2(z1, z2, nP12), g.t2xy);
+  g.t2yy = fma2(pt, fma2(z2, z2, nP22), g.t2yy);
+}
+
+template <int L>
+__device__ __forceinline__ void gal_single1(const float* __restrict__ c, const Offset& o,
+                                            GalSums1x2& g) {
+  GalSums1 h;
+#define GET(f) h.f = L ? g.f.y : g.f.x;
+#define PUT(f) (L ? g.f.y : g.f.x) = h.f;
+#define ALL(M) M(s0) M(s1x) M(s1y) M(t2xx) M(t2xy) M(t2yy)
+  ALL(GET)
+  gal_accumulate1(c, o, h);
+  ALL(PUT)
+#undef ALL
+#undef PUT
+#undef GET
 }
 
 // One pixel, value and gradient only (the adjoint of the pixel term through
@@ -401,20 +596,25 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
     sx = fmaf(phi, y1, sx);
     sy = fmaf(phi, y2, sy);
   }
-  GalSums1 ge = {}, gd = {};
+  GalSums1x2 g2 = {};
   const int per = ne + nd;
+  const int nb = ne < nd ? ne : nd;
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
     const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
     const Offset o = make_offset(dk[k]);
-    const int nb = ne < nd ? ne : nd;
-    for (int j = 0; j < nb; ++j) {
-      gal_accumulate1(base + j * kGalF, o, ge);
-      gal_accumulate1(base + (ne + j) * kGalF, o, gd);
-    }
-    for (int j = nb; j < ne; ++j) gal_accumulate1(base + j * kGalF, o, ge);
-    for (int j = nb; j < nd; ++j) gal_accumulate1(base + (ne + j) * kGalF, o, gd);
+    const Offset2 o2 = dup_offset(o);
+    for (int j = 0; j < nb; ++j) gal_accumulate1x2(base + j * 2 * kGalF, o2, g2);
+    const float* single = base + nb * 2 * kGalF;
+    for (int j = nb; j < ne; ++j, single += kGalF) gal_single1<0>(single, o, g2);
+    for (int j = nb; j < nd; ++j, single += kGalF) gal_single1<1>(single, o, g2);
   }
+  GalSums1 ge, gd;
+#define SPLIT(f) ge.f = g2.f.x; gd.f = g2.f.y;
+#define FLIP(f) ge.f = -g2.f.x; gd.f = -g2.f.y;        // first order: summed with -y
+  SPLIT(s0) FLIP(s1x) FLIP(s1y) SPLIT(t2xx) SPLIT(t2xy) SPLIT(t2yy)
+#undef FLIP
+#undef SPLIT
   const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
 #define MIX(f) fmaf(rho, ge.f, rho1 * gd.f)
   const float F0 = MIX(s0);
@@ -454,24 +654,56 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
   for (int g = 2; g < 6; ++g) acc[6 + g] = fmaf(cg, d0[g], acc[6 + g]);
 }
 
-// Writes the 64 warp-reduced sums of one item (lane a holds sums a, a + 32).
-__device__ __forceinline__ void reduce_store(float* __restrict__ acc, float* __restrict__ out,
-                                             int lane) {
+// Warp-shared memory of the derivative kernel: the staged record, then the
+// [kAcc][kHessRow] sums (rows 0..51 the Hessian sums, rows 52..63 the value
+// and gradient sums, written there for the final reduction).
+constexpr int kDerivWarpF = kDerivRecF + kAccTileF;
+
+// Adds the 64 sums of an item over the warp's lanes and writes them.  The
+// two value sums take the shuffle tree every pixel kernel uses for its value
+// sums, so that the value of an evaluation is the same in every pass (the
+// trust-region ratio compares values of the derivative and value passes);
+// for the other 62, lane l adds up rows (sums l and l + 32) along the
+// 33-float rows, in lane order, four chains per row.
+__device__ __forceinline__ void reduce_tile(float* __restrict__ tile, float* __restrict__ acc,
+                                            float* __restrict__ out, int lane) {
 #pragma unroll
-  for (int a = 0; a < kAcc; ++a) acc[a] = warp_sum(acc[a]);
+  for (int a = 2; a < kGradAcc; ++a) tile[(kHessAcc + a) * kHessRow + lane] = acc[a];
+  const float v0 = warp_sum(acc[0]), v1 = warp_sum(acc[1]);
+  if (lane == 0) {
+    out[0] = v0;
+    out[1] = v1;
+  }
+  __syncwarp();
 #pragma unroll
-  for (int a = 0; a < kAcc; ++a)
-    if ((a & 31) == lane) out[a] = acc[a];
+  for (int h = 0; h < 2; ++h) {
+    const int o = lane + 32 * h;
+    if (o < 2) continue;
+    const int row = o < kGradAcc ? kHessAcc + o : o - kGradAcc;
+    const float* r = tile + row * kHessRow;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; k += 4) {
+      c0 += r[k];
+      c1 += r[k + 1];
+      c2 += r[k + 2];
+      c3 += r[k + 3];
+    }
+    out[o] = (c0 + c1) + (c2 + c3);
+  }
 }
 
-// Three blocks per SM (168 registers a thread) keep 12 warps resident; the
-// few registers this costs spill outside the pixel loop.
-__global__ void __launch_bounds__(128, 3) derivs_kernel(PlanView v, int ne, int nd) {
+// Four blocks of four warps per SM: with the Hessian sums in shared memory
+// the kernel fits 128 registers a thread, and 16 warps keep the FP32 pipe
+// fed.
+__global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* rec = smem + wib * kDerivRecF;
+  float* rec = smem + wib * kDerivWarpF;
+  float* tile = rec + kDerivRecF;
+  const HessAcc hs{tile + lane};
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
@@ -479,20 +711,23 @@ __global__ void __launch_bounds__(128, 3) derivs_kernel(PlanView v, int ne, int 
     if (!v.active[pi.slot]) continue;
     __syncwarp();
     stage_record<true>(rec, v.records + (size_t)item.pair * kRecF,
-                       kPsf * (1 + ne + nd), lane);
-    __syncwarp();
-    float acc[kAcc];
+                       kPsf * (1 + ne + nd), lane, ne);
 #pragma unroll
-    for (int a = 0; a < kAcc; ++a) acc[a] = 0.f;
+    for (int a = 0; a < kHessAcc; ++a) tile[a * kHessRow + lane] = 0.f;
+    __syncwarp();
+    float acc[kGradAcc];
+#pragma unroll
+    for (int a = 0; a < kGradAcc; ++a) acc[a] = 0.f;
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
       const int qy = q / pi.w;
       const int qx = q - qy * pi.w;
       const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
       const float2 bg = v.bg[pi.bg_base + q];
-      pixel_derivs(rec, ne, nd, (float)qx, (float)qy, x, bg, acc);
+      pixel_derivs(rec, ne, nd, (float)qx, (float)qy, x, bg, acc, hs);
     }
-    reduce_store(acc, v.partials + (size_t)it * kAcc, lane);
+    __syncwarp();
+    reduce_tile(tile, acc, v.partials + (size_t)it * kAcc, lane);
   }
 }
 
@@ -509,7 +744,7 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
     if (!v.active[pi.slot]) continue;
     __syncwarp();
     stage_record<true>(rec, v.records + (size_t)item.pair * kRecF,
-                       kPsf * (1 + ne + nd), lane);
+                       kPsf * (1 + ne + nd), lane, ne);
     __syncwarp();
     float acc[kGradAcc];
 #pragma unroll
@@ -838,7 +1073,8 @@ __global__ void bg_scatter_kernel(PlanView v, float* bgE, float* bgV,
 }
 
 static size_t smem_bytes(int wpb) { return (size_t)wpb * kValRecF * sizeof(float); }
-static size_t smem_bytes_derivs(int wpb) { return (size_t)wpb * kDerivRecF * sizeof(float); }
+static size_t smem_bytes_derivs(int wpb) { return (size_t)wpb * kDerivWarpF * sizeof(float); }
+static size_t smem_bytes_grad(int wpb) { return (size_t)wpb * kDerivRecF * sizeof(float); }
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
@@ -857,7 +1093,7 @@ cudaError_t init_pixel_occupancy() {
                                                                   kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGrad], grad_kernel, kWpb * 32,
-                                                         smem_bytes_derivs(kWpb));
+                                                         smem_bytes_grad(kWpb));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValue], value_kernel, kWpb * 32, sm);
     if (e == cudaSuccess)
@@ -903,7 +1139,7 @@ cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
 
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes_derivs(kWpb),
+  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes_grad(kWpb),
                 L.stream>>>(
       v, L.n_exp, L.n_dev);
   return cudaGetLastError();
