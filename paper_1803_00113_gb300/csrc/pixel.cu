@@ -30,7 +30,8 @@ constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 // Every pixel kernel stages the (source, image) record of its work item in
 // the warp's shared memory, built from the global record (8 floats per
 // component: mx, my, P11, P12, P22, lw, tau) in one of two layouts:
-//   value layout:  header | origins | each component {A11, A12, A22, lw}
+//   value layout:  header | origins | star {A11, A12, A22, lw}
+//                                   | per PSF component k: galaxy pairs, then singles
 //   derivs layout: header | origins | star {A, lw | P, 0}
 //                                   | per PSF component k: galaxy pairs, then singles
 // A galaxy component has 16 values {A, lw | -P11, -P12, -P22, tau |
@@ -79,7 +80,28 @@ __device__ __forceinline__ void stage_record(float* __restrict__ dst, const floa
     const float p11 = a.z, p12 = a.w, p22 = b.x;
     const float4 q = quad_coeffs(p11, p12, p22, b.y);
     if (!kDerivs) {
-      d4[kCompBase / 4 + ci] = q;
+      if (ci < kPsf) {
+        d4[kCompBase / 4 + ci] = q;
+      } else {
+        // galaxy: pairs (exponential j, de Vaucouleurs j) interleaved, then
+        // the components without a partner
+        const int per = (n_comp - kPsf) / kPsf;
+        const int g = ci - kPsf, k = g / per, jj = g - k * per;
+        const int nb = n_exp < per - n_exp ? n_exp : per - n_exp;
+        const bool dev = jj >= n_exp;
+        const int j = dev ? jj - n_exp : jj;
+        float* base = dst + kCompBase + (kPsf + k * per) * kValF;
+        if (j < nb) {
+          float* o = base + j * 2 * kValF + (dev ? 1 : 0);
+          o[0] = q.x;
+          o[2] = q.y;
+          o[4] = q.z;
+          o[6] = q.w;
+        } else {
+          const int single = dev ? (n_exp - nb) + (j - nb) : j - nb;
+          *reinterpret_cast<float4*>(base + nb * 2 * kValF + single * kValF) = q;
+        }
+      }
     } else if (ci < kPsf) {
       float4* o = reinterpret_cast<float4*>(dst + kCompBase + ci * kStarF);
       o[0] = q;
@@ -273,27 +295,34 @@ __device__ __forceinline__ void gal_single(const float* __restrict__ c, const Of
 }
 
 // Galaxy (rho-mixed) and star profile densities of one pair at a pixel
-// (value layout).
+// (value layout): the galaxy pairs in packed two-wide instructions, the
+// exponential and de Vaucouleurs sums in the two halves (each half adds its
+// components in the order of the derivative kernel's sums).
 __device__ __forceinline__ void profiles_value(const float* __restrict__ rec, int ne, int nd,
                                                float px, float py, float& F0, float& F1) {
   const float4* q4 = reinterpret_cast<const float4*>(rec + kCompBase);
-  float fs = 0.f, fe = 0.f, fd = 0.f;
+  float fs = 0.f;
+  float2 f = make_float2(0.f, 0.f);
   const int per = ne + nd;
   const int nb = ne < nd ? ne : nd;
 #pragma unroll
   for (int k = 0; k < kPsf; ++k) {
     const Offset o = make_offset(pixel_delta(rec, k, px, py));
     fs += gauss_density(q4[k], o);
+    const Offset2 o2 = dup_offset(o);
     const float4* g = q4 + kPsf + k * per;
-    // the two profiles' sums are independent chains: interleave them
     for (int j = 0; j < nb; ++j) {
-      fe += gauss_density(g[j], o);
-      fd += gauss_density(g[ne + j], o);
+      const float4 a = g[2 * j], b = g[2 * j + 1];
+      const float2 arg = fma2(make_float2(a.x, a.y), o2.xx,
+                              fma2(make_float2(a.z, a.w), o2.xy,
+                                   fma2(make_float2(b.x, b.y), o2.yy, make_float2(b.z, b.w))));
+      f = add2(f, make_float2(exp2f(arg.x), exp2f(arg.y)));
     }
-    for (int j = nb; j < ne; ++j) fe += gauss_density(g[j], o);
-    for (int j = nb; j < nd; ++j) fd += gauss_density(g[ne + j], o);
+    const float4* single = g + 2 * nb;
+    for (int j = nb; j < ne; ++j) f.x += gauss_density(*single++, o);
+    for (int j = nb; j < nd; ++j) f.y += gauss_density(*single++, o);
   }
-  F0 = fmaf(rec[H_RHO], fe, rec[H_RHO1] * fd);
+  F0 = fmaf(rec[H_RHO], f.x, rec[H_RHO1] * f.y);
   F1 = fs;
 }
 
@@ -780,7 +809,7 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
     if (!v.active[pi.slot]) continue;
     __syncwarp();
     stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
-                        kPsf * (1 + ne + nd), lane);
+                        kPsf * (1 + ne + nd), lane, ne);
     __syncwarp();
     float rel = 0.f, base = 0.f;
     const int end = item.start + item.count;
@@ -822,22 +851,16 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
     if (!v.active[pi.slot]) continue;
     const celeste_image& im = v.images[pi.image];
     const int end = item.start + item.count;
-    for (int q = item.start + lane; q < end; q += 32) {
-      const int qy = q / pi.w;
-      const int qx = q - qy * pi.w;
-      const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
-      if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
-      v.bg[pi.bg_base + q] = make_float2(s, 0.f);
-    }
     if (v.cache) {
-      // gather the neighbours' cached moments (the values the render below
-      // would produce, added in the same order), 32 neighbour pairs at a
-      // time staged in the warp's shared memory
+      // sky plus the neighbours' cached moments (the values the render
+      // below would produce, added in the same order), 32 neighbour pairs
+      // at a time staged in the warp's shared memory; the first 32 are
+      // added in the pass that evaluates the sky
       int4* srect = reinterpret_cast<int4*>(rec);
       int64_t* soff = reinterpret_cast<int64_t*>(rec + 4 * 32);
       const int nn = pi.nbr_end - pi.nbr_begin;
-      for (int c0 = 0; c0 < nn; c0 += 32) {
-        const int cnt = min(32, nn - c0);
+      for (int c0 = 0; c0 == 0 || c0 < nn; c0 += 32) {
+        const int cnt = max(0, min(32, nn - c0));
         __syncwarp();
         if (lane < cnt) {
           const PairInfo qn = v.pairs[v.pair_nbr[pi.nbr_begin + c0 + lane]];
@@ -847,8 +870,16 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
         __syncwarp();
         for (int q = item.start + lane; q < end; q += 32) {
           const int qy = q / pi.w;
-          const int gx = pi.x0 + (q - qy * pi.w), gy = pi.y0 + qy;
-          float2 b = v.bg[pi.bg_base + q];
+          const int qx = q - qy * pi.w;
+          const int gx = pi.x0 + qx, gy = pi.y0 + qy;
+          float2 b;
+          if (c0 == 0) {
+            const float s = sky_value(im, v.sky, (float)gx, (float)gy);
+            if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
+            b = make_float2(s, 0.f);
+          } else {
+            b = v.bg[pi.bg_base + q];
+          }
           for (int k = 0; k < cnt; ++k) {
             const int4 r = srect[k];
             const int lx = gx - r.x, ly = gy - r.y;
@@ -862,12 +893,19 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
       }
       continue;
     }
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int qx = q - qy * pi.w;
+      const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
+      if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
+      v.bg[pi.bg_base + q] = make_float2(s, 0.f);
+    }
     for (int nb = pi.nbr_begin; nb < pi.nbr_end; ++nb) {
       const int np = v.pair_nbr[nb];
       const PairInfo qn = v.pairs[np];
       __syncwarp();
       stage_record<false>(rec, v.records + (size_t)np * kRecF,
-                          kPsf * (1 + ne + nd), lane);
+                          kPsf * (1 + ne + nd), lane, ne);
       __syncwarp();
       for (int q = item.start + lane; q < end; q += 32) {
         const int qy = q / pi.w;
@@ -902,7 +940,7 @@ __global__ void __launch_bounds__(128) render_kernel(PlanView v, int ne, int nd,
     const int64_t off = patches[pi.patch].pool_offset;
     __syncwarp();
     stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
-                        kPsf * (1 + ne + nd), lane);
+                        kPsf * (1 + ne + nd), lane, ne);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -933,7 +971,7 @@ __global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, i
     float2* out = v.cache + v.patches[pi.patch].pool_offset;
     __syncwarp();
     stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
-                        kPsf * (1 + ne + nd), lane);
+                        kPsf * (1 + ne + nd), lane, ne);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -947,16 +985,28 @@ __global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, i
   }
 }
 
-__global__ void commit_render_kernel(PlanView v, const int32_t* __restrict__ status) {
+// A copy: every lane loads up to eight pixels before it stores any, so that
+// enough loads are in flight to approach the copy bandwidth.
+__global__ void __launch_bounds__(128) commit_render_kernel(PlanView v,
+                                                            const int32_t* __restrict__ status) {
   const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int lane = threadIdx.x & 31;
   for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < v.n_items; it += nwarps) {
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (status[pi.source] != CELESTE_ST_ACCEPTED) continue;
-    float2* out = v.cache + v.patches[pi.patch].pool_offset;
-    for (int q = item.start + lane; q < item.start + item.count; q += 32)
-      out[q] = v.trial_render[pi.bg_base + q];
+    const float2* __restrict__ src = v.trial_render + pi.bg_base + item.start;
+    float2* __restrict__ dst = v.cache + v.patches[pi.patch].pool_offset + item.start;
+    const int n = item.count;
+    for (int q0 = lane; q0 < n; q0 += 8 * 32) {
+      float2 r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + 32 * u < n) r[u] = __ldcs(src + q0 + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + 32 * u < n) dst[q0 + 32 * u] = r[u];
+    }
   }
 }
 
@@ -976,7 +1026,7 @@ __global__ void __launch_bounds__(128) accumulate_kernel(PlanView v, int ne, int
     const PairInfo pi = v.pairs[item.pair];
     __syncwarp();
     stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
-                        kPsf * (1 + ne + nd), lane);
+                        kPsf * (1 + ne + nd), lane, ne);
     __syncwarp();
     const int end = item.start + item.count;
     for (int q = item.start + lane; q < end; q += 32) {
@@ -1080,7 +1130,7 @@ constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
 // Resident blocks per SM of each persistent pixel kernel, per device (0
 // until measured on that device).
-enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccKinds };
+enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccCommit, kOccKinds };
 static std::atomic<int> g_occ[kMaxDevices][kOccKinds] = {};
 static DeviceOnce g_occ_once;
 
@@ -1088,7 +1138,7 @@ cudaError_t init_pixel_occupancy() {
   return g_occ_once.run([] {
     const int dev = current_device();
     const size_t sm = smem_bytes(kWpb);
-    int occ[kOccKinds] = {0, 0, 0, 0, 0};
+    int occ[kOccKinds] = {0, 0, 0, 0, 0, 0};
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccDerivs], derivs_kernel,
                                                                   kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
@@ -1102,6 +1152,9 @@ cudaError_t init_pixel_occupancy() {
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccRender], render_cache_kernel,
                                                         kWpb * 32, sm);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccCommit], commit_render_kernel,
+                                                        kWpb * 32, 0);
     if (e == cudaSuccess)
       for (int k = 0; k < kOccKinds; ++k) g_occ[dev][k].store(occ[k], std::memory_order_relaxed);
     return e;
@@ -1154,7 +1207,8 @@ cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_re
 
 cudaError_t launch_commit_render(const Launch& L, const PlanView& v, const int32_t* status) {
   if (v.n_items == 0 || !v.cache || !v.trial_render) return cudaSuccess;
-  commit_render_kernel<<<grid_for(L, v.n_items, kWpb), kWpb * 32, 0, L.stream>>>(v, status);
+  commit_render_kernel<<<grid_for(L, v.n_items, kWpb, kOccCommit), kWpb * 32, 0, L.stream>>>(
+      v, status);
   return cudaGetLastError();
 }
 
