@@ -352,15 +352,18 @@ int celeste_field_elbo(celeste_ctx* ctx, celeste_field* field, double* out);
 /* ---- serving (region fits submitted by independent callers) ------------
  *
  * A server owns worker threads, each with its own context, stream and
- * resident device buffers.  celeste_submit validates a region request,
+ * resident device arenas.  celeste_submit validates a region request,
  * copies it (the caller's buffers may be reused as soon as it returns) and
- * queues it; a worker takes every queued request that fits its device
- * budget (device_bytes, estimated per request from its pixels, patches and
- * sources), lays them out as one problem and runs one fit over it in which
- * each request is a segment with its own passes and stopping rule (as
- * celeste_fit_run: max_passes, max_iter, pass_tol), so a request's result is
- * the same whether it ran alone or batched.  celeste_poll returns the result
- * once the request's segment has stopped.
+ * queues it.  Batching is continuous: a worker fits its running requests
+ * together, pass by pass, as one fit in which each request is a segment
+ * with its own passes and stopping rule (as celeste_fit_run: max_passes,
+ * max_iter, pass_tol), so a request's result is the same whether it ran
+ * alone or with others; after every pass it retires the requests whose
+ * segments stopped and admits queued requests, in order, while their
+ * footprint (device_bytes is the budget, estimated per request from its
+ * pixels, patches and sources) fits beside the running ones.  A request
+ * that arrives while others run thus starts at the next pass boundary.
+ * celeste_poll returns the result once the request's segment has stopped.
  *
  * Errors: celeste_submit returns CELESTE_EINVAL for a malformed request
  * (sizes, offsets, a patch outside its image, a neighbour index out of
@@ -372,7 +375,7 @@ int celeste_field_elbo(celeste_ctx* ctx, celeste_field* field, double* out);
  * its batch, e.g. CELESTE_EDEVICE when a device error bit was raised). */
 typedef struct celeste_server_config {
   int32_t workers;          /* worker threads (0 = 2) */
-  int32_t max_batch;        /* requests per batch (0 = no limit) */
+  int32_t max_batch;        /* running requests per worker (0 = no limit) */
   int64_t device_bytes;     /* per-worker budget of resident request data (0 = 4 GiB) */
   int64_t queue_bytes;      /* admission limit of queued requests (0 = 4 x budget x workers) */
   int32_t max_passes;       /* fit limits (0 = 5, 50) */
@@ -400,17 +403,21 @@ typedef struct celeste_region_request {
 typedef struct celeste_request_info {
   int32_t n_sources;
   int32_t passes;               /* passes the request's fit ran */
-  int32_t batch_requests;       /* requests in the batch it ran in */
+  int32_t batch_requests;       /* requests running beside it when it started, itself included */
   uint32_t device_error;        /* device error word of its batch (CELESTE_DERR_*) */
   double last_pass_gain;        /* ELBO gain of its last pass */
   double queue_s;               /* submit -> taken by a worker */
   double latency_s;             /* submit -> result ready */
+  double t_start_s, t_done_s;   /* taken by a worker, result ready: seconds on the
+                                   server's monotonic clock (comparable between
+                                   requests of one server) */
 } celeste_request_info;
 
 typedef struct celeste_server celeste_server;
 int celeste_server_create(const celeste_model* model, int device,
                           const celeste_server_config* config, celeste_server** out);
-/* Stops the workers after their current batch; queued requests are dropped. */
+/* Stops the workers after their current pass; queued and unfinished
+ * requests are dropped. */
 int celeste_server_destroy(celeste_server* server);
 int celeste_server_pause(celeste_server* server, int paused);
 int celeste_submit(celeste_server* server, const celeste_region_request* request,
@@ -420,7 +427,8 @@ int celeste_submit(celeste_server* server, const celeste_region_request* request
  * collected ticket is forgotten. */
 int celeste_poll(celeste_server* server, uint64_t ticket, int32_t wait_ms, double* theta_out,
                  int32_t* status_out, celeste_request_info* info);
-/* Kernel launches and batches so far; returns the first worker error. */
+/* Kernel launches so far and busy periods (a worker starting from no
+ * running request); returns the first worker error. */
 int celeste_server_stats(celeste_server* server, int64_t* launches, int64_t* batches);
 
 /* Only the FP64 trust-region subproblem, for n independent problems:

@@ -63,7 +63,8 @@ class _RequestInfo(ctypes.Structure):
     _fields_ = [("n_sources", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("batch_requests", ctypes.c_int32), ("device_error", ctypes.c_uint32),
                 ("last_pass_gain", ctypes.c_double), ("queue_s", ctypes.c_double),
-                ("latency_s", ctypes.c_double)]
+                ("latency_s", ctypes.c_double), ("t_start_s", ctypes.c_double),
+                ("t_done_s", ctypes.c_double)]
 
 
 class _Problem(ctypes.Structure):
@@ -693,7 +694,8 @@ class Server:
 
     def poll(self, ticket: int, wait_ms: int = 0):
         """None while the request runs; else a dict with theta [n, 27],
-        status [n], passes, latency_s, queue_s, batch_requests and code."""
+        status [n], passes, latency_s, queue_s, batch_requests, t_start_s,
+        t_done_s (the server's monotonic clock) and code."""
         if ticket not in self.sizes:
             raise CelesteError(f"unknown ticket {ticket}")
         n = self.sizes[ticket]
@@ -709,7 +711,8 @@ class Server:
         del self.sizes[ticket]
         return dict(theta=theta, status=status, passes=info.passes, latency_s=info.latency_s,
                     queue_s=info.queue_s, batch_requests=info.batch_requests,
-                    last_pass_gain=info.last_pass_gain, device_error=info.device_error, code=rc)
+                    last_pass_gain=info.last_pass_gain, device_error=info.device_error, code=rc,
+                    t_start_s=info.t_start_s, t_done_s=info.t_done_s)
 
     def stats(self):
         nl, nb = ctypes.c_int64(0), ctypes.c_int64(0)

@@ -1,20 +1,31 @@
 // Serving: region fits submitted by independent callers, batched on the GPU.
 //
 // A request is a small problem of its own (a sky region: its exposures and
-// the sources in it).  celeste_submit validates it, copies it and queues it;
-// worker threads (each with its own context, stream and resident buffers)
-// take every queued request that fits their device budget, lay the batch out
-// as one problem (the requests' images, patches and sources concatenated),
-// and run one segmented fit over it: each request is a segment with its own
-// pass count and stopping rule, so its result does not depend on what it
-// was batched with.  A request completes when its segment stops, possibly
-// before the rest of its batch; celeste_poll returns its result.
+// the sources in it).  celeste_submit validates it, copies it and queues it.
+// Each worker thread (its own context and stream) keeps a set of running
+// requests and fits them together: the running requests form one problem
+// (their images, patches and sources side by side) and one segmented fit in
+// which every request is a segment with its own pass count and stopping
+// rule, so its result does not depend on what it runs with.  Batching is
+// continuous: after every pass the worker retires the requests whose
+// segments stopped (their results are ready for celeste_poll at once) and
+// admits queued requests into the memory they and the still-running ones
+// leave free; a request that arrives while others are on the GPU starts at
+// the next pass boundary, not after the others finish.
+//
+// Every running request keeps fixed places in the worker's device arenas
+// (pixels, sky, render cache, a range of source ids for its parameters)
+// from admission to completion, so admitting others moves none of its data;
+// only the small tables that tie the running requests together (images,
+// patches, neighbour lists) are rebuilt, with a new fit, when the set of
+// running requests grows.
 #include <string.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -50,9 +61,53 @@ struct Request {
   uint32_t device_error = 0;
   int batch_requests = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
+  // places in the worker's arenas while running
+  int64_t pix_off = 0, sky_off = 0, cache_off = 0, n_pool = 0;
+  int src_first = 0;
+  int seg = -1;                      // segment in the worker's current fit
+  int passes_run = 0;                // passes run so far
 };
 
-// Grow-only device and pinned host buffers of a worker.
+// First-fit allocation of ranges of [0, cap) (host bookkeeping of a device
+// arena); freed ranges merge with their free neighbours.
+struct Arena {
+  int64_t cap = 0;
+  std::map<int64_t, int64_t> free_;  // offset -> length
+  void init(int64_t c) {
+    cap = c;
+    free_.clear();
+    if (c > 0) free_[0] = c;
+  }
+  int64_t alloc(int64_t n) {
+    if (n <= 0) return 0;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const int64_t off = it->first, len = it->second;
+      free_.erase(it);
+      if (len > n) free_[off + n] = len - n;
+      return off;
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t n) {
+    if (n <= 0) return;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+};
+
+// Grow-only device buffer.
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
@@ -61,7 +116,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
-    const size_t want = std::max(bytes, (size_t)1 << 20) + bytes / 4;
+    const size_t want = std::max(bytes, (size_t)1 << 16) + bytes / 4;
     if (cudaMalloc(&p, want) != cudaSuccess) return false;
     cap = want;
     return true;
@@ -70,25 +125,6 @@ struct DevBuf {
     if (p) cudaFree(p);
   }
 };
-struct HostBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  bool reserve(size_t bytes) {
-    if (bytes <= cap) return true;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-    const size_t want = std::max(bytes, (size_t)1 << 20) + bytes / 4;
-    if (cudaMallocHost(&p, want) != cudaSuccess) return false;
-    cap = want;
-    return true;
-  }
-  ~HostBuf() {
-    if (p) cudaFreeHost(p);
-  }
-};
-
-enum { kPix, kSky, kImg, kTheta, kPatchPtr, kPatch, kNbrPtr, kNbrIdx, kStatus, kCache, kBufs };
 
 }  // namespace
 
@@ -122,211 +158,343 @@ int64_t footprint(const Request& r) {
          32 * (int64_t)r.patches.size() + 12 * visits + 1792 * pairs + 16384 * (int64_t)r.n_sources;
 }
 
-// Runs one batch on a worker's context.  Returns an error code for the whole
-// batch (the requests then complete with it).
-int run_batch(celeste_server* S, celeste_ctx* ctx, cudaStream_t stream,
-              std::vector<std::shared_ptr<Request>>& batch, DevBuf* dev, HostBuf* host) {
-  const int R = (int)batch.size();
-  int64_t n_pix = 0, n_sky = 0;
-  int n_img = 0, n_src = 0, n_patch = 0, n_nbr = 0;
-  int64_t n_pool = 0;
-  for (auto& r : batch) {
-    for (const celeste_patch& q : r->patches) n_pool += (int64_t)q.w * q.h;
-    n_pix += (int64_t)r->pixels.size();
-    n_sky += (int64_t)r->sky.size();
-    n_img += (int)r->images.size();
-    n_src += r->n_sources;
-    n_patch += (int)r->patches.size();
-    n_nbr += (int)r->nbr_idx.size();
-  }
-  const size_t bytes[kBufs] = {(size_t)n_pix * 4,          (size_t)n_sky * 4,
-                               (size_t)n_img * sizeof(celeste_image),
-                               (size_t)n_src * CELESTE_N_THETA * 8,
-                               (size_t)(n_src + 1) * 4,     (size_t)n_patch * sizeof(celeste_patch),
-                               (size_t)(n_src + 1) * 4,     (size_t)n_nbr * 4,
-                               (size_t)n_src * 4,           (size_t)n_pool * 8};
-  for (int k = 0; k < kBufs; ++k)
-    if (!dev[k].reserve(bytes[k]) || (k != kCache && !host[k].reserve(bytes[k])))
-      return CELESTE_ENOMEM;
-  float* h_pix = static_cast<float*>(host[kPix].p);
-  float* h_sky = static_cast<float*>(host[kSky].p);
-  celeste_image* h_img = static_cast<celeste_image*>(host[kImg].p);
-  double* h_theta = static_cast<double*>(host[kTheta].p);
-  int32_t* h_pp = static_cast<int32_t*>(host[kPatchPtr].p);
-  celeste_patch* h_patch = static_cast<celeste_patch*>(host[kPatch].p);
-  int32_t* h_np = static_cast<int32_t*>(host[kNbrPtr].p);
-  int32_t* h_ni = static_cast<int32_t*>(host[kNbrIdx].p);
-  // concatenate: offsets of pixels, sky, images, sources and patches shift
-  std::vector<int32_t> seg_ptr(R + 1, 0), src_first(R, 0);
-  int64_t op = 0, os = 0, opool = 0;
-  int oi = 0, osrc = 0, opatch = 0, onbr = 0;
-  h_pp[0] = 0;
-  h_np[0] = 0;
-  for (int k = 0; k < R; ++k) {
-    const Request& r = *batch[k];
-    memcpy(h_pix + op, r.pixels.data(), r.pixels.size() * 4);
-    memcpy(h_sky + os, r.sky.data(), r.sky.size() * 4);
-    for (size_t i = 0; i < r.images.size(); ++i) {
-      celeste_image im = r.images[i];
-      im.pix_offset += op;
-      im.sky_offset += os;
-      h_img[oi + i] = im;
-    }
-    memcpy(h_theta + (size_t)osrc * CELESTE_N_THETA, r.theta.data(), r.theta.size() * 8);
-    for (int s = 0; s < r.n_sources; ++s) {
-      h_pp[osrc + s + 1] = opatch + r.patch_ptr[s + 1];
-      h_np[osrc + s + 1] = onbr + r.nbr_ptr[s + 1];
-    }
-    for (size_t q = 0; q < r.patches.size(); ++q) {
-      celeste_patch P = r.patches[q];
-      P.image += oi;
-      P.pool_offset = opool;
-      opool += (int64_t)P.w * P.h;
-      h_patch[opatch + q] = P;
-    }
-    for (size_t q = 0; q < r.nbr_idx.size(); ++q) h_ni[onbr + q] = r.nbr_idx[q] + osrc;
-    src_first[k] = osrc;
-    op += (int64_t)r.pixels.size();
-    os += (int64_t)r.sky.size();
-    oi += (int)r.images.size();
-    osrc += r.n_sources;
-    opatch += (int)r.patches.size();
-    onbr += (int)r.nbr_idx.size();
-    seg_ptr[k + 1] = osrc;
-  }
-  for (int k = 0; k < kStatus; ++k)
-    if (bytes[k]) CK(cudaMemcpyAsync(dev[k].p, host[k].p, bytes[k], cudaMemcpyHostToDevice, stream));
+// A worker: its context, its arenas and the requests it is running.
+struct Worker {
+  celeste_server* S = nullptr;
+  celeste_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  // device arenas: pixels and sky (floats), render cache (float2 per patch
+  // pixel), parameters (27 doubles per source id)
+  float* d_pix = nullptr;
+  float* d_sky = nullptr;
+  float* d_cache = nullptr;
+  double* d_theta = nullptr;
+  Arena a_pix, a_sky, a_cache, a_src;
+  // tables of the running set (host copies, read by plan creation, and
+  // their device copies)
+  std::vector<celeste_image> h_img;
+  std::vector<celeste_patch> h_patch;
+  std::vector<int32_t> h_pp, h_np, h_ni;
+  DevBuf d_img, d_patch, d_pp, d_np, d_ni, d_status;
+  std::vector<double> h_theta;
+  std::vector<int32_t> h_status;
+  std::vector<std::shared_ptr<Request>> run;   // running requests, segment order
   celeste_problem P{};
-  P.pixels = static_cast<const float*>(dev[kPix].p);
-  P.sky = static_cast<const float*>(dev[kSky].p);
-  P.images = static_cast<const celeste_image*>(dev[kImg].p);
-  P.theta = static_cast<double*>(dev[kTheta].p);
-  P.patch_ptr = static_cast<const int32_t*>(dev[kPatchPtr].p);
-  P.patches = static_cast<const celeste_patch*>(dev[kPatch].p);
-  P.nbr_ptr = static_cast<const int32_t*>(dev[kNbrPtr].p);
-  P.nbr_idx = static_cast<const int32_t*>(dev[kNbrIdx].p);
-  P.h_patch_ptr = h_pp;
-  P.h_patches = h_patch;
-  P.h_images = h_img;
-  P.h_nbr_ptr = h_np;
-  P.h_nbr_idx = h_ni;
-  P.n_pixels = n_pix;
-  P.n_sky = n_sky;
-  P.n_pool = n_pool;
-  P.render_cache = static_cast<float*>(dev[kCache].p);
-  P.n_images = n_img;
-  P.n_sources = n_src;
-  P.n_patches = n_patch;
-  P.n_nbr = n_nbr;
-  std::vector<int32_t> ids(n_src);
-  for (int s = 0; s < n_src; ++s) ids[s] = s;
   celeste_fit* F = nullptr;
-  celeste_tuning tuning{};
-  tuning.pixels_per_item = S->cfg.pixels_per_item;
-  int rc = fit_create_segments(ctx, &P, ids.data(), n_src, seg_ptr.data(), R, &tuning, &F);
-  if (rc) return rc;
-  rc = fit_begin(ctx, F, S->cfg.max_passes, S->cfg.max_iter, S->cfg.pass_tol);
-  std::vector<char> finished(R, 0);
-  double* h_th = static_cast<double*>(host[kTheta].p);
-  int32_t* h_st = static_cast<int32_t*>(host[kStatus].p);
-  const int64_t l0 = ctx ? celeste_launch_count(ctx) : 0;
-  int active = R, guard = 0;
-  while (rc == CELESTE_OK && active > 0 && guard++ < F->f.max_passes) {
-    rc = fit_pass(ctx, F, &active);
-    if (rc) break;
-    // read back every request whose segment just stopped
-    std::vector<int> now_done;
-    for (int k = 0; k < R; ++k)
-      if (!finished[k] && (!F->h_seg_active[k] || active == 0)) now_done.push_back(k);
-    for (int k : now_done) {
-      const Request& r = *batch[k];
-      const size_t o = (size_t)src_first[k];
-      rc = cudaMemcpyAsync(h_th + o * CELESTE_N_THETA, P.theta + o * CELESTE_N_THETA,
-                           (size_t)r.n_sources * CELESTE_N_THETA * 8, cudaMemcpyDeviceToHost,
-                           stream) == cudaSuccess &&
-                   cudaMemcpyAsync(h_st + o, F->f.status + o, (size_t)r.n_sources * 4,
-                                   cudaMemcpyDeviceToHost, stream) == cudaSuccess
-               ? CELESTE_OK
-               : CELESTE_ECUDA;
-      if (rc) break;
+  int64_t run_bytes = 0;
+
+  ~Worker() {
+    if (F) celeste_fit_destroy(F);
+    for (void* q : {(void*)d_pix, (void*)d_sky, (void*)d_cache, (void*)d_theta})
+      if (q) cudaFree(q);
+    if (ctx) celeste_destroy(ctx);
+    if (stream) cudaStreamDestroy(stream);
+  }
+
+  int init() {
+    CK(cudaSetDevice(S->device));
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    int rc = celeste_create(&ctx, &S->model, S->device, stream);
+    if (rc) return rc;
+    // capacities: a request's footprint counts 4 bytes per pixel, 8 bytes of
+    // cache per patch pixel among its 12 per visit, and 16 KiB per source,
+    // so arenas of the budget's size hold every admissible set
+    const int64_t B = S->cfg.device_bytes;
+    a_pix.init(B / 4);
+    a_sky.init(std::max<int64_t>(B / 64, 1024));
+    a_cache.init(B / 8);
+    a_src.init(std::max<int64_t>(B / 16384, 64));
+    if (cudaMalloc(&d_pix, a_pix.cap * 4) != cudaSuccess ||
+        cudaMalloc(&d_sky, a_sky.cap * 4) != cudaSuccess ||
+        cudaMalloc(&d_cache, a_cache.cap * 8) != cudaSuccess ||
+        cudaMalloc(&d_theta, a_src.cap * CELESTE_N_THETA * 8) != cudaSuccess)
+      return CELESTE_ENOMEM;
+    return CELESTE_OK;
+  }
+
+  // Places r in the arenas; false (nothing held) when a range does not fit.
+  bool place(Request& r) {
+    int64_t pool = 0;
+    for (const celeste_patch& q : r.patches) pool += (int64_t)q.w * q.h;
+    const int64_t op = a_pix.alloc((int64_t)r.pixels.size());
+    const int64_t os = op < 0 ? -1 : a_sky.alloc((int64_t)r.sky.size());
+    const int64_t oc = os < 0 ? -1 : a_cache.alloc(pool);
+    const int64_t of = oc < 0 ? -1 : a_src.alloc(r.n_sources);
+    if (of < 0) {
+      if (oc >= 0) a_cache.release(oc, pool);
+      if (os >= 0) a_sky.release(os, (int64_t)r.sky.size());
+      if (op >= 0) a_pix.release(op, (int64_t)r.pixels.size());
+      return false;
     }
-    if (rc == CELESTE_OK && !now_done.empty()) {
-      uint32_t word = 0;
-      const int sync = celeste_synchronize(ctx, &word);
-      const double t = now_s();
-      std::lock_guard<std::mutex> lk(S->mu);
-      for (int k : now_done) {
-        Request& r = *batch[k];
-        const size_t o = (size_t)src_first[k];
-        r.theta_out.assign(h_th + o * CELESTE_N_THETA, h_th + (o + r.n_sources) * CELESTE_N_THETA);
-        r.status_out.assign(h_st + o, h_st + o + r.n_sources);
-        r.passes = F->h_seg_passes[k];
-        r.last_gain = F->h_seg_gain[k];
-        r.batch_requests = R;
-        r.error = sync;
-        r.device_error = word;
-        r.t_done = t;
-        r.state = 2;
-        finished[k] = 1;
+    r.pix_off = op;
+    r.sky_off = os;
+    r.cache_off = oc;
+    r.n_pool = pool;
+    r.src_first = (int)of;
+    return true;
+  }
+
+  void unplace(const Request& r) {
+    a_pix.release(r.pix_off, (int64_t)r.pixels.size());
+    a_sky.release(r.sky_off, (int64_t)r.sky.size());
+    a_cache.release(r.cache_off, r.n_pool);
+    a_src.release(r.src_first, r.n_sources);
+  }
+
+  // Uploads a newly placed request's pixels, sky and initial parameters.
+  int upload(const Request& r) {
+    CK(cudaMemcpyAsync(d_pix + r.pix_off, r.pixels.data(), r.pixels.size() * 4,
+                       cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_sky + r.sky_off, r.sky.data(), r.sky.size() * 4, cudaMemcpyHostToDevice,
+                       stream));
+    CK(cudaMemcpyAsync(d_theta + (size_t)r.src_first * CELESTE_N_THETA, r.theta.data(),
+                       r.theta.size() * 8, cudaMemcpyHostToDevice, stream));
+    return CELESTE_OK;
+  }
+
+  // Tables of the running set and a fit over it (segments in run order);
+  // continuing requests keep their pass counts.
+  int rebuild() {
+    if (F) {
+      celeste_fit_destroy(F);
+      F = nullptr;
+    }
+    // source ids in use: [0, n_ids); ids no running request holds are empty
+    int n_ids = 0;
+    for (auto& r : run) n_ids = std::max(n_ids, r->src_first + r->n_sources);
+    std::vector<const Request*> by_id(n_ids, nullptr);
+    for (auto& r : run)
+      for (int s = 0; s < r->n_sources; ++s) by_id[r->src_first + s] = r.get();
+    h_img.clear();
+    std::unordered_map<const Request*, int> img_base;
+    for (auto& r : run) {
+      img_base[r.get()] = (int)h_img.size();
+      for (celeste_image im : r->images) {
+        im.pix_offset += r->pix_off;
+        im.sky_offset += r->sky_off;
+        h_img.push_back(im);
       }
-      S->cv_done.notify_all();
     }
+    h_patch.clear();
+    h_ni.clear();
+    h_pp.assign(n_ids + 1, 0);
+    h_np.assign(n_ids + 1, 0);
+    std::unordered_map<const Request*, int64_t> pool_at;
+    for (int id = 0; id < n_ids; ++id) {
+      const Request* r = by_id[id];
+      if (r) {
+        const int s = id - r->src_first;
+        int64_t& pool = pool_at[r];          // running pool offset within the request
+        if (s == 0) pool = 0;
+        for (int q = r->patch_ptr[s]; q < r->patch_ptr[s + 1]; ++q) {
+          celeste_patch P = r->patches[q];
+          P.image += img_base[r];
+          P.pool_offset = r->cache_off + pool;
+          pool += (int64_t)P.w * P.h;
+          h_patch.push_back(P);
+        }
+        for (int k = r->nbr_ptr[s]; k < r->nbr_ptr[s + 1]; ++k)
+          h_ni.push_back(r->nbr_idx[k] + r->src_first);
+      }
+      h_pp[id + 1] = (int32_t)h_patch.size();
+      h_np[id + 1] = (int32_t)h_ni.size();
+    }
+    if (h_ni.empty()) h_ni.push_back(0);
+    if (!d_img.reserve(h_img.size() * sizeof(celeste_image)) ||
+        !d_patch.reserve(std::max<size_t>(h_patch.size(), 1) * sizeof(celeste_patch)) ||
+        !d_pp.reserve(h_pp.size() * 4) || !d_np.reserve(h_np.size() * 4) ||
+        !d_ni.reserve(h_ni.size() * 4) || !d_status.reserve((size_t)std::max(n_ids, 1) * 4))
+      return CELESTE_ENOMEM;
+    CK(cudaMemcpyAsync(d_img.p, h_img.data(), h_img.size() * sizeof(celeste_image),
+                       cudaMemcpyHostToDevice, stream));
+    if (!h_patch.empty())
+      CK(cudaMemcpyAsync(d_patch.p, h_patch.data(), h_patch.size() * sizeof(celeste_patch),
+                         cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_pp.p, h_pp.data(), h_pp.size() * 4, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_np.p, h_np.data(), h_np.size() * 4, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_ni.p, h_ni.data(), h_ni.size() * 4, cudaMemcpyHostToDevice, stream));
+    P = celeste_problem{};
+    P.pixels = d_pix;
+    P.sky = d_sky;
+    P.images = static_cast<const celeste_image*>(d_img.p);
+    P.theta = d_theta;
+    P.patch_ptr = static_cast<const int32_t*>(d_pp.p);
+    P.patches = static_cast<const celeste_patch*>(d_patch.p);
+    P.nbr_ptr = static_cast<const int32_t*>(d_np.p);
+    P.nbr_idx = static_cast<const int32_t*>(d_ni.p);
+    P.h_patch_ptr = h_pp.data();
+    P.h_patches = h_patch.data();
+    P.h_images = h_img.data();
+    P.h_nbr_ptr = h_np.data();
+    P.h_nbr_idx = h_ni.data();
+    P.n_pixels = a_pix.cap;
+    P.n_sky = a_sky.cap;
+    P.n_pool = a_cache.cap;
+    P.render_cache = d_cache;
+    P.n_images = (int32_t)h_img.size();
+    P.n_sources = n_ids;
+    P.n_patches = (int32_t)h_patch.size();
+    P.n_nbr = (int32_t)(h_ni.size() == 1 && h_np[n_ids] == 0 ? 0 : h_ni.size());
+    std::vector<int32_t> ids, seg_ptr(1, 0);
+    std::vector<int32_t> passes;
+    for (auto& r : run) {
+      r->seg = (int)passes.size();
+      for (int s = 0; s < r->n_sources; ++s) ids.push_back(r->src_first + s);
+      seg_ptr.push_back((int32_t)ids.size());
+      passes.push_back(r->passes_run);
+    }
+    celeste_tuning tuning{};
+    tuning.pixels_per_item = S->cfg.pixels_per_item;
+    int rc = fit_create_segments(ctx, &P, ids.data(), (int)ids.size(), seg_ptr.data(),
+                                 (int)run.size(), &tuning, &F);
+    if (rc) return rc;
+    rc = fit_begin(ctx, F, S->cfg.max_passes, S->cfg.max_iter, S->cfg.pass_tol);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(F->f.seg_passes, passes.data(), passes.size() * 4, cudaMemcpyHostToDevice,
+                       stream));
+    return CELESTE_OK;
   }
-  {
+
+  // Completes requests (under the server lock): result or error.
+  void complete(const std::vector<std::shared_ptr<Request>>& done, int err, uint32_t word) {
+    const double t = now_s();
     std::lock_guard<std::mutex> lk(S->mu);
-    S->launches += celeste_launch_count(ctx) - l0;
-    ++S->batches;
+    for (auto& r : done) {
+      r->error = err;
+      r->device_error = word;
+      r->t_done = t;
+      r->state = 2;
+    }
+    S->cv_done.notify_all();
   }
-  celeste_fit_destroy(F);
-  return rc;
-}
+
+  // One pass of the running set; retires the requests whose segments
+  // stopped (their results read back and published).
+  int pass() {
+    int n_active = 0;
+    int rc = fit_pass(ctx, F, &n_active);
+    if (rc) return rc;
+    std::vector<std::shared_ptr<Request>> done;
+    std::vector<std::shared_ptr<Request>> keep;
+    for (size_t k = 0; k < run.size(); ++k) {
+      Request& r = *run[k];
+      r.passes_run = F->h_seg_passes[r.seg];
+      r.last_gain = F->h_seg_gain[r.seg];
+      if (F->h_seg_active[r.seg]) {
+        keep.push_back(run[k]);
+        continue;
+      }
+      r.theta_out.resize((size_t)r.n_sources * CELESTE_N_THETA);
+      r.status_out.resize(r.n_sources);
+      CK(cudaMemcpyAsync(r.theta_out.data(), d_theta + (size_t)r.src_first * CELESTE_N_THETA,
+                         r.theta_out.size() * 8, cudaMemcpyDeviceToHost, stream));
+      CK(cudaMemcpyAsync(r.status_out.data(), F->f.status + r.src_first, (size_t)r.n_sources * 4,
+                         cudaMemcpyDeviceToHost, stream));
+      r.passes = r.passes_run;
+      done.push_back(run[k]);
+    }
+    if (done.empty()) return CELESTE_OK;
+    uint32_t word = 0;
+    const int sync = celeste_synchronize(ctx, &word);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto& r : done) {
+        unplace(*r);
+        run_bytes -= r->bytes;
+      }
+    }
+    complete(done, sync, word);
+    // the fit keeps the finished segments frozen until the next rebuild
+    run.swap(keep);
+    return CELESTE_OK;
+  }
+};
 
 void worker_main(celeste_server* S) {
-  cudaSetDevice(S->device);
-  cudaStream_t stream = nullptr;
-  celeste_ctx* ctx = nullptr;
-  int rc = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess
-               ? celeste_create(&ctx, &S->model, S->device, stream)
-               : CELESTE_ECUDA;
-  DevBuf dev[kBufs];
-  HostBuf host[kBufs];
+  Worker W;
+  W.S = S;
+  const int init_rc = W.init();
   for (;;) {
-    std::vector<std::shared_ptr<Request>> batch;
+    std::vector<std::shared_ptr<Request>> admitted;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || (!S->paused && !S->queue.empty()); });
+      S->cv_work.wait(lk, [&] {
+        return S->stop || !W.run.empty() || (!S->paused && !S->queue.empty());
+      });
       if (S->stop) break;
-      int64_t bytes = 0;
+      // admission: queued requests in order, while their footprint fits the
+      // budget beside the running ones and the arenas have room
       const double t = now_s();
-      while (!S->queue.empty()) {
+      while (!S->paused && !S->queue.empty() && init_rc == CELESTE_OK) {
         auto& r = S->queue.front();
-        if (!batch.empty() && (bytes + r->bytes > S->cfg.device_bytes ||
-                               (S->cfg.max_batch > 0 && (int)batch.size() >= S->cfg.max_batch)))
+        if (S->cfg.max_batch > 0 && (int)(W.run.size() + admitted.size()) >= S->cfg.max_batch)
           break;
-        bytes += r->bytes;
+        if (W.run_bytes + r->bytes > S->cfg.device_bytes) break;
+        if (!W.place(*r)) break;
+        W.run_bytes += r->bytes;
         S->queued_bytes -= r->bytes;
         r->state = 1;
         r->t_start = t;
-        batch.push_back(r);
+        admitted.push_back(r);
+        S->queue.pop_front();
+      }
+      if (init_rc != CELESTE_OK && !S->queue.empty()) {
+        // a worker that could not start fails what it takes
+        admitted.push_back(S->queue.front());
         S->queue.pop_front();
       }
     }
-    int brc = rc ? rc : run_batch(S, ctx, stream, batch, dev, host);
-    if (brc) {
+    if (init_rc != CELESTE_OK) {
+      W.complete(admitted, init_rc, 0);
       std::lock_guard<std::mutex> lk(S->mu);
-      const double t = now_s();
-      for (auto& r : batch)
-        if (r->state != 2) {
-          r->error = brc;
-          r->t_done = t;
-          r->state = 2;
+      if (S->worker_error == CELESTE_OK) S->worker_error = init_rc;
+      continue;
+    }
+    int rc = CELESTE_OK;
+    const bool fresh = W.run.empty() && !admitted.empty();
+    if (!admitted.empty()) {
+      for (auto& r : admitted) {
+        if (rc == CELESTE_OK) rc = W.upload(*r);
+        W.run.push_back(r);
+      }
+      const int n_run = (int)W.run.size();
+      for (auto& r : admitted) r->batch_requests = n_run;
+      if (rc == CELESTE_OK) rc = W.rebuild();
+      if (fresh) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->batches;
+      }
+    }
+    const int64_t l0 = celeste_launch_count(W.ctx);
+    if (rc == CELESTE_OK && !W.run.empty()) rc = W.pass();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->launches += celeste_launch_count(W.ctx) - l0;
+    }
+    if (rc != CELESTE_OK) {
+      // the running requests fail with the error; the worker starts afresh
+      std::vector<std::shared_ptr<Request>> failed;
+      failed.swap(W.run);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto& r : failed) {
+          W.unplace(*r);
+          W.run_bytes -= r->bytes;
         }
-      if (S->worker_error == CELESTE_OK) S->worker_error = brc;
-      S->cv_done.notify_all();
+        if (S->worker_error == CELESTE_OK) S->worker_error = rc;
+      }
+      W.complete(failed, rc, 0);
+      if (W.F) {
+        celeste_fit_destroy(W.F);
+        W.F = nullptr;
+      }
+      continue;
+    }
+    if (W.run.empty() && W.F) {
+      celeste_fit_destroy(W.F);
+      W.F = nullptr;
     }
   }
-  if (ctx) celeste_destroy(ctx);
-  if (stream) cudaStreamDestroy(stream);
 }
 
 bool valid_request(const celeste_region_request* q) {
@@ -462,6 +630,8 @@ int celeste_poll(celeste_server* S, uint64_t ticket, int32_t wait_ms, double* th
     info->last_pass_gain = r->last_gain;
     info->queue_s = r->t_start - r->t_submit;
     info->latency_s = r->t_done - r->t_submit;
+    info->t_start_s = r->t_start;
+    info->t_done_s = r->t_done;
   }
   const int err = r->error;
   S->tickets.erase(it);

@@ -54,6 +54,33 @@ def test_request_result_equals_the_region_fit(cel):
     assert np.array_equal(r["status"], st)
 
 
+def test_a_request_arriving_mid_run_joins_at_a_pass_boundary(cel):
+    """Continuous batching: a request submitted while another runs is
+    admitted before that one finishes, and its result is bitwise the one it
+    gets alone."""
+    import time
+    big = fields.region_request(777, n_sources=64, side=400)
+    small = fields.region_request(702, n_sources=2, side=40)
+    srv = cel.Server(small.model, workers=1)
+    alone = _collect(srv, [srv.submit(small)]).popitem()[1]
+    srv.close()
+    srv = cel.Server(big.model, workers=1)
+    t_big = srv.submit(big)
+    time.sleep(0.02)                       # the big request is on the GPU
+    t_small = srv.submit(small)
+    res = _collect(srv, [t_small, t_big])
+    srv.close()
+    b, s = res[t_big], res[t_small]
+    assert b["passes"] >= 2
+    # admitted after the big request started and before it finished ...
+    assert b["t_start_s"] < s["t_start_s"] < b["t_done_s"]
+    assert s["batch_requests"] == 2
+    # ... with the result it has alone
+    assert s["passes"] == alone["passes"]
+    assert np.array_equal(s["theta"], alone["theta"])
+    assert np.array_equal(s["status"], alone["status"])
+
+
 def test_alone_equals_batched_with_others(cel):
     reqs = _requests()
     alone = {}
@@ -62,7 +89,8 @@ def test_alone_equals_batched_with_others(cel):
         alone[k] = _collect(srv, [srv.submit(q)]).popitem()[1]
         assert alone[k]["batch_requests"] == 1
     srv.close()
-    # the same requests queued together run as one batch (one segmented fit)
+    # the same requests queued together start as one running set (one
+    # segmented fit; requests leave it as their segments stop)
     srv = cel.Server(reqs[0].model, workers=1, start_paused=True)
     order = [2, 0, 3, 1]
     tickets = {k: srv.submit(reqs[k]) for k in order}
