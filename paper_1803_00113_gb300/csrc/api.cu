@@ -70,14 +70,16 @@ bool spd_inverse4(const double C[4][4], double P[4][4], double* logdet) {
 template <typename T>
 T* dev_alloc(celeste_plan* p, size_t count, int* err) {
   if (count == 0) count = 1;
-  void* ptr = nullptr;
-  if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) {
+  void* ptr = ctx_alloc(p->ctx, false, count * sizeof(T));
+  if (!ptr) {
     *err = CELESTE_ENOMEM;
     return nullptr;
   }
   p->allocs.push_back(ptr);
   return static_cast<T*>(ptr);
 }
+
+
 
 // Runs one launch, bracketed by a pair of events when profiling (under
 // stream capture an ordinary record only expresses a dependency; the
@@ -124,6 +126,83 @@ int run_setup(celeste_ctx* c, celeste_plan* p, int first, int n, bool trial) {
 }  // namespace
 
 namespace celeste {
+
+// ---- memory pools of contexts --------------------------------------------
+
+void* MemPool::get(bool host, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto& fr = free_[host];
+    auto it = fr.lower_bound(bytes);
+    if (it != fr.end() && it->first <= 2 * bytes) {
+      void* ptr = it->second;
+      fr.erase(it);
+      return ptr;
+    }
+  }
+  void* ptr = nullptr;
+  const cudaError_t e = host ? cudaMallocHost(&ptr, bytes) : cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu_);
+  size_[host][ptr] = bytes;
+  return ptr;
+}
+
+void MemPool::put(bool host, void* ptr) {
+  if (!ptr) return;
+  std::lock_guard<std::mutex> lk(mu_);
+  auto it = size_[host].find(ptr);
+  if (it != size_[host].end()) free_[host].emplace(it->second, ptr);
+}
+
+// Frees the cached blocks.  Blocks still held by plans or fits stay theirs:
+// they go straight back to CUDA when those are destroyed.
+void MemPool::release_all() {
+  std::lock_guard<std::mutex> lk(mu_);
+  for (int h = 0; h < 2; ++h) {
+    for (auto& kv : free_[h]) {
+      if (h) cudaFreeHost(kv.second);
+      else cudaFree(kv.second);
+    }
+    size_[h].clear();
+    free_[h].clear();
+  }
+}
+
+namespace {
+// Live contexts by serial: plans and fits may outlive their context.
+std::mutex g_ctx_mu;
+std::unordered_map<uint64_t, celeste_ctx*> g_ctx_live;
+uint64_t g_ctx_serial = 0;
+}  // namespace
+
+void* ctx_alloc(celeste_ctx* c, bool host, size_t bytes) {
+  return c->pool.get(host, bytes);
+}
+
+void ctx_release(celeste_ctx* c, uint64_t serial, bool host,
+                          const std::vector<void*>& blocks) {
+  bool live = false;
+  {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    auto it = g_ctx_live.find(serial);
+    live = it != g_ctx_live.end() && it->second == c;
+  }
+  if (live) {
+    // the blocks may still be read by work queued on the context's stream
+    // (destroying a context while another thread destroys its plans is a
+    // caller error, as for any object in use)
+    cudaStreamSynchronize(c->stream);
+    for (void* b : blocks) c->pool.put(host, b);
+    return;
+  }
+  for (void* b : blocks) {
+    if (host) cudaFreeHost(b);
+    else cudaFree(b);
+  }
+}
 
 bool prepare_model(const celeste_model* m, ModelDev* md) {
   if (m->n_exp < 1 || m->n_exp > kMaxProf || m->n_dev < 1 || m->n_dev > kMaxProf ||
@@ -231,6 +310,11 @@ int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* 
   CK(cudaSetDevice(device));
   celeste_ctx* c = new celeste_ctx();
   c->device = device;
+  {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    c->serial = ++g_ctx_serial;
+    g_ctx_live[c->serial] = c;
+  }
   c->stream = static_cast<cudaStream_t>(stream);
   c->n_exp = m->n_exp;
   c->n_dev = m->n_dev;
@@ -242,6 +326,10 @@ int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* 
       cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
     cudaFree(c->d_model);
     cudaFree(c->d_err);
+    {
+      std::lock_guard<std::mutex> lk(g_ctx_mu);
+      g_ctx_live.erase(c->serial);
+    }
     delete c;
     return CELESTE_ECUDA;
   }
@@ -252,6 +340,12 @@ int celeste_create(celeste_ctx** out, const celeste_model* m, int device, void* 
 int celeste_destroy(celeste_ctx* c) {
   if (!c) return CELESTE_EINVAL;
   cudaSetDevice(c->device);
+  {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    g_ctx_live.erase(c->serial);
+  }
+  cudaStreamSynchronize(c->stream);
+  c->pool.release_all();
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   cudaFree(c->d_model);
   cudaFree(c->d_err);
@@ -374,55 +468,69 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   }
   const int n_own = (int)pairs.size();
   // neighbour pairs: (neighbour source, its patch in the same image) that
-  // overlap an own patch
+  // overlap an own patch.  Per own source, each patch of each neighbour is
+  // matched to the own pairs in its image; every own pair lists its
+  // neighbour pairs in (neighbour, patch) order.
   std::unordered_map<int64_t, int> nb_index;
-  for (int pp = 0; pp < n_own; ++pp) {
-    const PairInfo pi = pairs[pp];   // a copy: pairs grows inside the loop
-    pairs[pp].nbr_begin = (int)pair_nbr.size();
-    const int s = pi.source;
+  std::vector<std::vector<int32_t>> per_pair(n_own);
+  std::unordered_map<int32_t, std::vector<int32_t>> own_in_image;
+  for (int j = 0; j < n; ++j) {
+    const int s = ids[j];
+    own_in_image.clear();
+    for (int pp = slot_ptr[j]; pp < slot_ptr[j + 1]; ++pp) own_in_image[pairs[pp].image].push_back(pp);
     for (int k = pr->h_nbr_ptr[s]; k < pr->h_nbr_ptr[s + 1]; ++k) {
       const int t = pr->h_nbr_idx[k];
       if (t < 0 || t >= pr->n_sources) return CELESTE_EINVAL;
       for (int q = pr->h_patch_ptr[t]; q < pr->h_patch_ptr[t + 1]; ++q) {
         const celeste_patch& P = pr->h_patches[q];
-        if (P.image != pi.image) continue;
+        auto own = own_in_image.find(P.image);
+        if (own == own_in_image.end()) continue;
         if (!patch_ok(P)) return CELESTE_EINVAL;
-        if (P.x0 >= pi.x0 + pi.w || pi.x0 >= P.x0 + P.w || P.y0 >= pi.y0 + pi.h || pi.y0 >= P.y0 + P.h)
-          continue;
-        const int64_t key = (int64_t)t * (int64_t)pr->n_patches + q;
-        auto it = nb_index.find(key);
-        int idx;
-        if (it == nb_index.end()) {
-          idx = (int)pairs.size();
-          nb_index.emplace(key, idx);
-          const celeste_image& im = pr->h_images[P.image];
-          PairInfo qn{};
-          qn.source = t;
-          qn.slot = -1;
-          qn.patch = q;
-          qn.image = P.image;
-          qn.x0 = P.x0;
-          qn.y0 = P.y0;
-          qn.w = P.w;
-          qn.h = P.h;
-          qn.pix_base = im.pix_offset + (int64_t)P.y0 * im.row_stride + P.x0;
-          qn.stride = im.row_stride;
-          qn.band = im.band;
-          qn.bg_base = -1;
-          qn.nbr_begin = qn.nbr_end = 0;
-          qn.item_begin = qn.item_end = 0;
-          pairs.push_back(qn);
-        } else {
-          idx = it->second;
+        for (const int32_t pp : own->second) {
+          const PairInfo pi = pairs[pp];   // a copy: pairs grows below
+          if (P.x0 >= pi.x0 + pi.w || pi.x0 >= P.x0 + P.w || P.y0 >= pi.y0 + pi.h ||
+              pi.y0 >= P.y0 + P.h)
+            continue;
+          const int64_t key = (int64_t)t * (int64_t)pr->n_patches + q;
+          auto it = nb_index.find(key);
+          int idx;
+          if (it == nb_index.end()) {
+            idx = (int)pairs.size();
+            nb_index.emplace(key, idx);
+            const celeste_image& im = pr->h_images[P.image];
+            PairInfo qn{};
+            qn.source = t;
+            qn.slot = -1;
+            qn.patch = q;
+            qn.image = P.image;
+            qn.x0 = P.x0;
+            qn.y0 = P.y0;
+            qn.w = P.w;
+            qn.h = P.h;
+            qn.pix_base = im.pix_offset + (int64_t)P.y0 * im.row_stride + P.x0;
+            qn.stride = im.row_stride;
+            qn.band = im.band;
+            qn.bg_base = -1;
+            qn.nbr_begin = qn.nbr_end = 0;
+            qn.item_begin = qn.item_end = 0;
+            pairs.push_back(qn);
+          } else {
+            idx = it->second;
+          }
+          per_pair[pp].push_back(idx);
         }
-        pair_nbr.push_back(idx);
       }
     }
+  }
+  for (int pp = 0; pp < n_own; ++pp) {
+    pairs[pp].nbr_begin = (int)pair_nbr.size();
+    pair_nbr.insert(pair_nbr.end(), per_pair[pp].begin(), per_pair[pp].end());
     pairs[pp].nbr_end = (int)pair_nbr.size();
   }
 
   celeste_plan* p = new celeste_plan();
   p->ctx = c;
+  p->ctx_serial = c->serial;
   p->visits = visits;
   if (tuning) p->tuning = *tuning;
   p->tuning.pixels_per_item = ppi;
@@ -489,7 +597,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
 
 int celeste_plan_destroy(celeste_plan* p) {
   if (!p) return CELESTE_EINVAL;
-  for (void* a : p->allocs) cudaFree(a);
+  ctx_release(p->ctx, p->ctx_serial, false, p->allocs);
   delete p;
   return CELESTE_OK;
 }

@@ -13,6 +13,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 
 #include "host.h"
 
@@ -157,17 +159,40 @@ int fit_create_segments(celeste_ctx* c, const celeste_problem* pr, const int32_t
   }
   celeste_fit* F = new celeste_fit();
   F->ctx = c;
+  F->ctx_serial = c->serial;
   F->region.assign(ids, ids + n);
   F->seg_ptr.assign(seg_ptr, seg_ptr + n_seg + 1);
   F->n_sources = pr->n_sources;
   int rc = CELESTE_OK;
-  for (int col = 0; col < n_colors && rc == CELESTE_OK; ++col) {
-    std::vector<int32_t> cls;
-    for (int s : sorted)
-      if (color[s] == col) cls.push_back(s);
-    celeste_plan* p = nullptr;
-    rc = celeste_plan_create(c, pr, cls.data(), (int)cls.size(), tuning, &p);
-    if (rc == CELESTE_OK) F->plans.push_back(p);
+  // one plan per colour class; the classes are planned on parallel host
+  // threads (planning is host work proportional to the class's pixels)
+  std::vector<std::vector<int32_t>> cls(n_colors);
+  for (int s : sorted) cls[color[s]].push_back(s);
+  std::vector<celeste_plan*> plans(n_colors, nullptr);
+  std::vector<int> rcs(n_colors, CELESTE_OK);
+  int device = 0;
+  cudaGetDevice(&device);
+  auto plan_class = [&](int col) {
+    cudaSetDevice(device);
+    rcs[col] = celeste_plan_create(c, pr, cls[col].data(), (int)cls[col].size(), tuning,
+                                   &plans[col]);
+  };
+  const int n_threads =
+      std::min<int>(n_colors, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+  if (n_threads <= 1) {
+    for (int col = 0; col < n_colors; ++col) plan_class(col);
+  } else {
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int t = 0; t < n_threads; ++t)
+      pool.emplace_back([&] {
+        for (int col; (col = next.fetch_add(1)) < n_colors;) plan_class(col);
+      });
+    for (auto& t : pool) t.join();
+  }
+  for (int col = 0; col < n_colors; ++col) {
+    if (rcs[col] != CELESTE_OK && rc == CELESTE_OK) rc = rcs[col];
+    if (plans[col]) F->plans.push_back(plans[col]);
   }
   if (rc == CELESTE_OK && pr->render_cache) {
     // sources outside the region that border it: rendered into the cache
@@ -186,9 +211,9 @@ int fit_create_segments(celeste_ctx* c, const celeste_problem* pr, const int32_t
       rc = celeste_plan_create(c, pr, outside.data(), (int)outside.size(), tuning, &F->outside);
   }
   auto alloc = [&](size_t bytes) -> void* {
-    void* ptr = nullptr;
     if (rc != CELESTE_OK) return nullptr;
-    if (cudaMalloc(&ptr, bytes ? bytes : 1) != cudaSuccess) {
+    void* ptr = ctx_alloc(c, false, bytes);
+    if (!ptr) {
       rc = CELESTE_ENOMEM;
       return nullptr;
     }
@@ -196,12 +221,13 @@ int fit_create_segments(celeste_ctx* c, const celeste_problem* pr, const int32_t
     return ptr;
   };
   auto pinned = [&](size_t bytes) -> void* {
-    void* ptr = nullptr;
     if (rc != CELESTE_OK) return nullptr;
-    if (cudaMallocHost(&ptr, bytes ? bytes : 1) != cudaSuccess) {
+    void* ptr = ctx_alloc(c, true, bytes);
+    if (!ptr) {
       rc = CELESTE_ENOMEM;
       return nullptr;
     }
+    F->host_allocs.push_back(ptr);
     return ptr;
   };
   const size_t S = (size_t)pr->n_sources;
@@ -373,9 +399,8 @@ int fit_begin(celeste_ctx* c, celeste_fit* F, int max_passes, int max_iter, doub
   return CELESTE_OK;
 }
 
-int fit_pass(celeste_ctx* c, celeste_fit* F, int* n_active) {
+int fit_pass_launch(celeste_ctx* c, celeste_fit* F) {
   const FitView& f = F->f;
-  *n_active = 0;
   if (f.n_region == 0) return CELESTE_OK;
   CK(cudaGraphLaunch(F->exec, c->stream));
   CK(cudaMemcpyAsync(F->h_summary, f.summary, (1 + f.n_classes) * sizeof(int32_t),
@@ -385,6 +410,20 @@ int fit_pass(celeste_ctx* c, celeste_fit* F, int* n_active) {
                      c->stream));
   CK(cudaMemcpyAsync(F->h_seg_passes, f.seg_passes, f.n_seg * sizeof(int32_t),
                      cudaMemcpyDeviceToHost, c->stream));
+  return CELESTE_OK;
+}
+
+int fit_pass(celeste_ctx* c, celeste_fit* F, int* n_active) {
+  *n_active = 0;
+  const int rc = fit_pass_launch(c, F);
+  if (rc) return rc;
+  return fit_pass_finish(c, F, n_active);
+}
+
+int fit_pass_finish(celeste_ctx* c, celeste_fit* F, int* n_active) {
+  const FitView& f = F->f;
+  *n_active = 0;
+  if (f.n_region == 0) return CELESTE_OK;
   CK(cudaStreamSynchronize(c->stream));
   // launches of the pass: reset and summary, per class 3 + the loop trips
   int64_t nl = 2;
@@ -407,12 +446,10 @@ int celeste_fit_destroy(celeste_fit* F) {
   if (F->exec) cudaGraphExecDestroy(F->exec);
   if (F->graph) cudaGraphDestroy(F->graph);
   if (F->capture) cudaStreamDestroy(F->capture);
-  for (void* h : {(void*)F->h_summary, (void*)F->h_seg_active, (void*)F->h_seg_gain,
-                  (void*)F->h_seg_passes})
-    if (h) cudaFreeHost(h);
   for (celeste_plan* p : F->plans) celeste_plan_destroy(p);
   if (F->outside) celeste_plan_destroy(F->outside);
-  for (void* a : F->allocs) cudaFree(a);
+  ctx_release(F->ctx, F->ctx_serial, true, F->host_allocs);
+  ctx_release(F->ctx, F->ctx_serial, false, F->allocs);
   delete F;
   return CELESTE_OK;
 }

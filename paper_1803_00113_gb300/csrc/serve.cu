@@ -182,8 +182,22 @@ struct Worker {
   celeste_problem P{};
   celeste_fit* F = nullptr;
   int64_t run_bytes = 0;
+  // destroys the fit a rebuild replaced while the next pass runs (tearing
+  // down a fit's graph and plans takes milliseconds of host time)
+  std::thread reaper;
+
+  void reap(celeste_fit* old) {
+    if (reaper.joinable()) reaper.join();
+    if (!old) return;
+    const int dev = S->device;
+    reaper = std::thread([old, dev] {
+      cudaSetDevice(dev);
+      celeste_fit_destroy(old);
+    });
+  }
 
   ~Worker() {
+    if (reaper.joinable()) reaper.join();
     if (F) celeste_fit_destroy(F);
     for (void* q : {(void*)d_pix, (void*)d_sky, (void*)d_cache, (void*)d_theta})
       if (q) cudaFree(q);
@@ -255,10 +269,8 @@ struct Worker {
   // Tables of the running set and a fit over it (segments in run order);
   // continuing requests keep their pass counts.
   int rebuild() {
-    if (F) {
-      celeste_fit_destroy(F);
-      F = nullptr;
-    }
+    reap(F);
+    F = nullptr;
     // source ids in use: [0, n_ids); ids no running request holds are empty
     int n_ids = 0;
     for (auto& r : run) n_ids = std::max(n_ids, r->src_first + r->n_sources);
