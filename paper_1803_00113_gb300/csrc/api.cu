@@ -607,7 +607,9 @@ int64_t celeste_plan_visits(const celeste_plan* p) { return p ? p->visits : -1; 
 static int eval_common(celeste_ctx* c, celeste_plan* p, bool derivs) {
   Launch L = make_launch(c, p);
   CK(cudaMemsetAsync(p->v.active, 1, p->v.n > 0 ? p->v.n : 1, c->stream));
-  int rc = run_setup(c, p, 0, p->v.n_pairs, false);
+  // with a render cache the background comes from cached moments, so only
+  // the own pairs need records
+  int rc = run_setup(c, p, 0, p->v.cache ? p->v.n_own_pairs : p->v.n_pairs, false);
   if (rc) return rc;
   c->launches += 2;
   CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, p->v); }));
@@ -683,7 +685,9 @@ int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, i
   PlanView& v = p->v;
   c->launches += 1;
   CK(timed(c, CELESTE_K_OTHER, 0, L.stream, [&] { return launch_mark_active(L, v, status); }));
-  int rc = run_setup(c, p, 0, v.n_pairs, false);
+  // with a render cache the background comes from cached moments, so only
+  // the own pairs need records
+  int rc = run_setup(c, p, 0, v.cache ? v.n_own_pairs : v.n_pairs, false);
   if (rc) return rc;
   c->launches += 3;
   CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, v); }));

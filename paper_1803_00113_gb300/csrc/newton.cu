@@ -45,9 +45,19 @@ constexpr int kTri = N * (N + 1) / 2;                        // 378 lower entrie
 
 struct TrSmem {
   double B[N * N];
-  // mixed-precision path
-  double W[N * N];                 // factorisation work copy of B + l I
-  double L[N * N];                 // unit lower factor of B + l I (strict lower part)
+  // mixed-precision path.  The FP32 reduction (Bf), then locate32's
+  // per-thread elimination factors (cps, gps: [i][thread]), then the FP64
+  // factorisations (W, L) use the same memory in turn.
+  union Work {
+    struct Fp64 {
+      double W[N * N];             // factorisation work copy of B + l I
+      double L[N * N];             // unit lower factor of B + l I (strict lower part)
+      float Bf[N * N];             // FP32 copy of B, reduced to tridiagonal form
+    } f;
+    struct Sec {
+      float cps[N * kTrThreads], gps[N * kTrThreads];
+    } s;
+  } ws;
   double Dinv[32];                 // 1 / D
   double col[2][32];               // published pivot column, double-buffered
   double p[32];
@@ -57,9 +67,9 @@ struct TrSmem {
   int positive;                    // FP32 finds B positive definite
   int tried0;                      // l = 0 has been evaluated
   int bisects;                     // bisection steps of the FP64 iteration
-  float Bf[N * N];
   float betaf[32], dfr[32], efr[32], gfr[32];
-  float cps[N * 32], gps[N * 32];  // per-lane scratch of the FP32 secular solves ([i][lane])
+  float loc[4];                    // locate32: scale, |g|^2 (scaled), |p(0)|^2
+  unsigned hmask[2][4];            // locate32: probe ballots of the four warps
   short2 tri[kTri];                // lower entry e -> (row, column)
   int mode;                        // 0 interior candidate, 1 boundary, 2 full FP64 path
   double beta[32];
@@ -154,8 +164,8 @@ __device__ __noinline__ float norm2_32(const float* d, const float* e, const flo
   return s;
 }
 
-// |y|^2 for (T + lam I) y = g in FP32 with the per-lane elimination
-// factors in shared memory (cps, gps: [i][lane] layout, lane's column).
+// |y|^2 for (T + lam I) y = g in FP32 with the per-thread elimination
+// factors in shared memory (cps, gps: [i][thread] layout, the thread's column).
 __device__ float norm2_32s(const float* d, const float* e, const float* g, float lam, float* cps,
                            float* gps) {
   float m = d[0] + lam;
@@ -168,12 +178,12 @@ __device__ float norm2_32s(const float* d, const float* e, const float* g, float
     r = __fdividef(1.f, m);
     c = i < N - 1 ? e[i] * r : 0.f;
     gp = (g[i] - e[i - 1] * gp) * r;
-    cps[i * 32] = c;
-    gps[i * 32] = gp;
+    cps[i * kTrThreads] = c;
+    gps[i * kTrThreads] = gp;
   }
   float y = gp, sum = y * y;
   for (int i = N - 2; i >= 0; --i) {
-    y = gps[i * 32] - cps[i * 32] * y;
+    y = gps[i * kTrThreads] - cps[i * kTrThreads] * y;
     sum += y * y;
   }
   return sum;
@@ -546,13 +556,13 @@ __device__ __forceinline__ double pivot_rcp(double d) {
 // pivot applied on the fly; thread 0, which updates the next diagonal entry
 // first, takes its reciprocal right away.  The columns of L are scaled at
 // the end.  Returns false (the same on every thread) when a pivot is not
-// positive.  On success S.L holds the unit lower factor (strictly lower
-// part) and S.Dinv the inverse pivots.  S.W is the working copy.
+// positive.  On success S.ws.f.L holds the unit lower factor (strictly
+// lower part) and S.Dinv the inverse pivots.  S.ws.f.W is the working copy.
 __device__ bool ldl_factor(TrSmem& S, double lam) {
   const int tid = threadIdx.x;
   for (int e = tid; e < kTri; e += kTrThreads) {
     const short2 t = S.tri[e];
-    S.W[t.x * N + t.y] = S.B[t.x * N + t.y] + (t.x == t.y ? lam : 0.0);
+    S.ws.f.W[t.x * N + t.y] = S.B[t.x * N + t.y] + (t.x == t.y ? lam : 0.0);
   }
   if (tid == 0) S.Dinv[0] = pivot_rcp(B_diag0(S, lam));
   if (__syncthreads_or(tid == 0 && S.Dinv[0] == 0.0)) return false;
@@ -564,8 +574,8 @@ __device__ bool ldl_factor(TrSmem& S, double lam) {
     for (int e = tid; e < cnt; e += kTrThreads) {
       const short2 t = S.tri[e];                  // (row, col) in the trailing block
       const int i = j + 1 + t.x, k = j + 1 + t.y;
-      const double w = fma(-(S.W[i * N + j] * dinv), S.W[k * N + j], S.W[i * N + k]);
-      S.W[i * N + k] = w;
+      const double w = fma(-(S.ws.f.W[i * N + j] * dinv), S.ws.f.W[k * N + j], S.ws.f.W[i * N + k]);
+      S.ws.f.W[i * N + k] = w;
       if (e == 0) {                               // the next pivot
         const double r = pivot_rcp(w);
         S.Dinv[j + 1] = r;
@@ -576,7 +586,7 @@ __device__ bool ldl_factor(TrSmem& S, double lam) {
   }
   for (int e = tid; e < kTri; e += kTrThreads) {
     const short2 t = S.tri[e];
-    if (t.x > t.y) S.L[t.x * N + t.y] = S.W[t.x * N + t.y] * S.Dinv[t.y];
+    if (t.x > t.y) S.ws.f.L[t.x * N + t.y] = S.ws.f.W[t.x * N + t.y] * S.Dinv[t.y];
   }
   __syncthreads();
   return true;
@@ -590,12 +600,12 @@ __device__ double ldl_solve_full(TrSmem& S, const double* rhs, double* out, int 
   double b = lane < N ? rhs[lane] : 0.0;
   for (int k = 0; k < N - 1; ++k) {
     const double wk = __shfl_sync(0xffffffffu, b, k);
-    if (lane > k && lane < N) b = fma(-S.L[lane * N + k], wk, b);
+    if (lane > k && lane < N) b = fma(-S.ws.f.L[lane * N + k], wk, b);
   }
   double z = lane < N ? b * S.Dinv[lane] : 0.0;
   for (int k = N - 1; k > 0; --k) {
     const double pk = __shfl_sync(0xffffffffu, z, k);
-    if (lane < k) z = fma(-S.L[k * N + lane], pk, z);
+    if (lane < k) z = fma(-S.ws.f.L[k * N + lane], pk, z);
   }
   if (lane < N) out[lane] = z;
   const double n2 = warp_sum_d(z * z);
@@ -603,7 +613,7 @@ __device__ double ldl_solve_full(TrSmem& S, const double* rhs, double* out, int 
     double u = z;
     for (int k = 0; k < N - 1; ++k) {
       const double uk = __shfl_sync(0xffffffffu, u, k);
-      if (lane > k && lane < N) u = fma(-S.L[lane * N + k], uk, u);
+      if (lane > k && lane < N) u = fma(-S.ws.f.L[lane * N + k], uk, u);
     }
     *q2 = warp_sum_d(lane < N ? u * u * S.Dinv[lane] : 0.0);
     if (lane < N) S.z[lane] = u;        // u = L^{-1} p, for first_order()
@@ -618,13 +628,13 @@ __device__ void first_order(TrSmem& S, int lane, double dl) {
   double z = lane < N ? S.z[lane] * S.Dinv[lane] : 0.0;
   for (int k = N - 1; k > 0; --k) {
     const double qk = __shfl_sync(0xffffffffu, z, k);
-    if (lane < k) z = fma(-S.L[k * N + lane], qk, z);
+    if (lane < k) z = fma(-S.ws.f.L[k * N + lane], qk, z);
   }
   if (lane < N) S.p[lane] = fma(-dl, z, S.p[lane]);
   __syncwarp();
 }
 
-// Householder reduction of B (FP32, in S.Bf) to tridiagonal form by all
+// Householder reduction of B (FP32, in S.ws.f.Bf) to tridiagonal form by all
 // four warps: thread t owns row t / 4 of the trailing block and, in it, the
 // columns c = t (mod 4); two block barriers per reflection.  Every warp
 // reduces the pivot column itself (rows on lanes, the same shuffle tree in
@@ -633,7 +643,7 @@ __device__ void first_order(TrSmem& S, int lane, double dl) {
 __device__ void householder_blk(TrSmem& S) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int i = tid >> 2, sub = tid & 3;
-  float* Bf = S.Bf;
+  float* Bf = S.ws.f.Bf;
   float gi = i < N ? S.gfr[i] : 0.f;
   for (int k = 0; k < N - 2; ++k) {
     const float xl = (lane > k && lane < N) ? Bf[lane * N + k] : 0.f;
@@ -703,55 +713,78 @@ __device__ void householder_blk(TrSmem& S) {
   __syncthreads();
 }
 
-// Warp 0: from the FP32 tridiagonal form, lambda_min and the multiplier to
-// FP32 accuracy; sets S.mode, S.lam, S.lo, S.hi (unscaled).
-__device__ void locate32(TrSmem& S, double Delta) {
-  const int lane = threadIdx.x & 31;
-  float rowf = 0.f, g2f = 0.f;
-  if (lane < N) {
-    rowf = fabsf(S.dfr[lane]) + fabsf(S.efr[lane]) + (lane ? fabsf(S.efr[lane - 1]) : 0.f);
-    g2f = S.gfr[lane] * S.gfr[lane];
-  }
+// The first of the block's 127 probes (threads 0..126) that is set, or 127
+// when none is; one barrier (the ballot slots alternate between rounds).
+__device__ __forceinline__ int first_hit(TrSmem& S, bool hit, int round) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, hit && tid < kTrThreads - 1);
+  if (lane == 0) S.hmask[round & 1][wid] = m;
+  __syncthreads();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rowf = fmaxf(rowf, __shfl_xor_sync(0xffffffffu, rowf, o));
-    g2f += __shfl_xor_sync(0xffffffffu, g2f, o);
+  for (int w = 0; w < kTrThreads / 32; ++w) {
+    const unsigned mw = S.hmask[round & 1][w];
+    if (mw) return w * 32 + __ffs(mw) - 1;
   }
-  const float scale = fmaxf(rowf, 1e-30f);
+  return kTrThreads - 1;
+}
+
+// All four warps: from the FP32 tridiagonal form, lambda_min and the
+// multiplier to FP32 accuracy by multisection, 127 probes a round (7 bits);
+// sets S.mode, S.lam, S.lo, S.hi (unscaled).
+__device__ void locate32(TrSmem& S, double Delta) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr float kStep = 1.f / (float)kTrThreads;
+  if (wid == 0) {
+    float rowf = 0.f, g2f = 0.f;
+    if (lane < N) {
+      rowf = fabsf(S.dfr[lane]) + fabsf(S.efr[lane]) + (lane ? fabsf(S.efr[lane - 1]) : 0.f);
+      g2f = S.gfr[lane] * S.gfr[lane];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rowf = fmaxf(rowf, __shfl_xor_sync(0xffffffffu, rowf, o));
+      g2f += __shfl_xor_sync(0xffffffffu, g2f, o);
+    }
+    const float scale = fmaxf(rowf, 1e-30f);
+    const float inv = 1.f / scale;
+    if (lane < N) {
+      S.df[lane] = S.dfr[lane] * inv;
+      S.ef[lane] = S.efr[lane] * inv;
+      S.e2f[lane] = S.ef[lane] * S.ef[lane];
+      S.gf[lane] = S.gfr[lane] * inv;
+    }
+    if (lane == 0) {
+      S.loc[0] = scale;
+      S.loc[1] = g2f;
+    }
+  }
+  __syncthreads();
+  const float scale = S.loc[0], g2f = S.loc[1];
   const float inv = 1.f / scale;
-  if (lane < N) {
-    S.df[lane] = S.dfr[lane] * inv;
-    S.ef[lane] = S.efr[lane] * inv;
-    S.e2f[lane] = S.ef[lane] * S.ef[lane];
-    S.gf[lane] = S.gfr[lane] * inv;
-  }
-  __syncwarp();
+  float* cps = S.ws.s.cps + tid;
+  float* gps = S.ws.s.gps + tid;
   const float gnorm_s = sqrtf(g2f) * inv;
   const float D2 = (float)(Delta * Delta);
-  float fa, fb;
-  {
-    fa = -1.f - 1e-6f;
-    fb = 1.f + 1e-6f;
-    for (int round = 0; round < 5; ++round) {
-      const float sig = fa + (fb - fa) * (float)(lane + 1) * (1.f / 32.f);
-      const bool hit = lane < 31 && sturm32s(S.df, S.e2f, sig) >= 1;
-      const unsigned mask = __ballot_sync(0xffffffffu, hit);
-      const int t = mask ? __ffs(mask) - 1 : 31;
-      const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * (1.f / 32.f);
-      const float nb = t == 31 ? fb : fa + (fb - fa) * (float)(t + 1) * (1.f / 32.f);
-      fa = na;
-      fb = nb;
-    }
+  int round = 0;
+  float fa = -1.f - 1e-6f, fb = 1.f + 1e-6f;
+  for (int r = 0; r < 4; ++r, ++round) {
+    const float sig = fa + (fb - fa) * (float)(tid + 1) * kStep;
+    const int t = first_hit(S, sturm32s(S.df, S.e2f, sig) >= 1, round);
+    const float na = t == 0 ? fa : fa + (fb - fa) * (float)t * kStep;
+    const float nb = t == kTrThreads - 1 ? fb : fa + (fb - fa) * (float)(t + 1) * kStep;
+    fa = na;
+    fb = nb;
   }
   // lambda_min (scaled) lies in [fa, fb] up to FP32 rounding of the counts
   const float lmin = fa;
+  if (tid == 0) S.loc[2] = lmin > 0.f ? norm2_32s(S.df, S.ef, S.gf, 0.f, cps, gps) : 3.4e38f;
+  __syncthreads();
+  const float n0 = S.loc[2];
   // mode 0: try l = 0 first (interior Newton step); mode 1: the boundary
   // root from the bracket [la, lb]; mode 2: the all-FP64 path
   int mode = 1;
   float la = 0.f, lb = 0.f;
   bool bracket = false;
-  const float n0 = lmin > 0.f ? norm2_32s(S.df, S.ef, S.gf, 0.f, S.cps + lane, S.gps + lane)
-                              : 3.4e38f;
   if (!(g2f > 0.f)) {
     mode = 2;
   } else if (lmin > 1e-4f && n0 <= D2 * 0.999f) {
@@ -765,13 +798,12 @@ __device__ void locate32(TrSmem& S, double Delta) {
     const float lo = fmaxf(0.f, -lmin);
     la = lo;
     lb = lo + gnorm_s / (float)Delta * 1.01f + 1e-6f;
-    for (int round = 0; round < 6; ++round) {
-      const float l = la + (lb - la) * (float)(lane + 1) * (1.f / 32.f);
-      const bool inside = lane < 31 && norm2_32s(S.df, S.ef, S.gf, l, S.cps + lane, S.gps + lane) <= D2;
-      const unsigned mask = __ballot_sync(0xffffffffu, inside);
-      const int t = mask ? __ffs(mask) - 1 : 31;
-      const float na = t == 0 ? la : la + (lb - la) * (float)t * (1.f / 32.f);
-      const float nb = t == 31 ? lb : la + (lb - la) * (float)(t + 1) * (1.f / 32.f);
+    for (int r = 0; r < 4; ++r, ++round) {
+      const float l = la + (lb - la) * (float)(tid + 1) * kStep;
+      const bool inside = tid < kTrThreads - 1 && norm2_32s(S.df, S.ef, S.gf, l, cps, gps) <= D2;
+      const int t = first_hit(S, inside, round);
+      const float na = t == 0 ? la : la + (lb - la) * (float)t * kStep;
+      const float nb = t == kTrThreads - 1 ? lb : la + (lb - la) * (float)(t + 1) * kStep;
       la = na;
       lb = nb;
     }
@@ -779,7 +811,7 @@ __device__ void locate32(TrSmem& S, double Delta) {
     // start; the FP64 iteration below resolves it, and a true hard case
     // (no root above the pole) ends in the all-FP64 path
   }
-  if (lane == 0) {
+  if (tid == 0) {
     S.mode = mode;
     const double sc = (double)scale;
     S.lmin_lo = (double)scale * (double)fa;
@@ -793,7 +825,7 @@ __device__ void locate32(TrSmem& S, double Delta) {
     S.lo = -1.0;                      // FP64 bounds: none yet
     S.hi = -1.0;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // Exact trust-region subproblem of one source; 128 threads (4 warps) enter,
@@ -806,11 +838,13 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
     const int i = e / N, j = e % N;
     const double b = -0.5 * (H[i * N + j] + H[j * N + i]);
     S.B[e] = b;
-    S.Bf[e] = (float)b;
+    S.ws.f.Bf[e] = (float)b;
   }
   for (int e = tid; e < kTri; e += kTrThreads) {
-    int i = 0;
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    // row i of lower entry e: i (i + 1) / 2 <= e < (i + 1) (i + 2) / 2
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if (i * (i + 1) / 2 > e) --i;
+    if ((i + 1) * (i + 2) / 2 <= e) ++i;
     S.tri[e] = make_short2((short)i, (short)(e - i * (i + 1) / 2));
   }
   if (tid < N) {
@@ -819,8 +853,7 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
   }
   __syncthreads();
   householder_blk(S);
-  if (wid == 0) locate32(S, Delta);
-  __syncthreads();
+  locate32(S, Delta);
   const double D2 = Delta * Delta;
   bool done = false;
   if (S.mode != 2) {

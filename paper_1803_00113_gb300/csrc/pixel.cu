@@ -688,6 +688,7 @@ __device__ __forceinline__ void pixel_grad(const float* __restrict__ rec, int ne
 // and gradient sums, written there for the final reduction).
 constexpr int kDerivWarpF = kDerivRecF + kAccTileF;
 
+
 // Adds the 64 sums of an item over the warp's lanes and writes them.  The
 // two value sums take the shuffle tree every pixel kernel uses for its value
 // sums, so that the value of an evaluation is the same in every pass (the
@@ -724,7 +725,9 @@ __device__ __forceinline__ void reduce_tile(float* __restrict__ tile, float* __r
 
 // Four blocks of four warps per SM: with the Hessian sums in shared memory
 // the kernel fits 128 registers a thread, and 16 warps keep the FP32 pipe
-// fed.
+// fed.  (Forming the background here instead of in background_kernel was
+// measured slower: the cached-moment loads inside the pixel loop stall 16
+// warps more than a separate kernel's many warps.)
 __global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -836,6 +839,33 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
   }
 }
 
+// Stages neighbour pairs [c0, c0 + cnt) of own pair pi: rectangle and offset
+// of the neighbour's patch in the render cache.
+__device__ __forceinline__ void stage_neighbours(const PlanView& v, const PairInfo& pi, int c0,
+                                                 int cnt, int4* srect, int64_t* soff, int lane) {
+  if (lane < cnt) {
+    const PairInfo qn = v.pairs[v.pair_nbr[pi.nbr_begin + c0 + lane]];
+    srect[lane] = make_int4(qn.x0, qn.y0, qn.w, qn.h);
+    soff[lane] = v.patches[qn.patch].pool_offset;
+  }
+}
+
+// Adds the cached moments of the staged neighbours whose patches hold the
+// pixel (gx, gy) of the image, in staging order.
+__device__ __forceinline__ float2 add_neighbours(const PlanView& v, float2 b, int gx, int gy,
+                                                 int cnt, const int4* srect,
+                                                 const int64_t* soff) {
+  for (int k = 0; k < cnt; ++k) {
+    const int4 r = srect[k];
+    const int lx = gx - r.x, ly = gy - r.y;
+    if (lx < 0 || ly < 0 || lx >= r.z || ly >= r.w) continue;
+    const float2 c = v.cache[soff[k] + ly * r.z + lx];
+    b.x += c.x;
+    b.y += c.y;
+  }
+  return b;
+}
+
 // Background of every own patch pixel: sky plus each neighbour's E and V
 // where the pixel lies in that neighbour's patch (support rule, Sec. 2.2.3).
 __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int nd) {
@@ -862,11 +892,7 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
       for (int c0 = 0; c0 == 0 || c0 < nn; c0 += 32) {
         const int cnt = max(0, min(32, nn - c0));
         __syncwarp();
-        if (lane < cnt) {
-          const PairInfo qn = v.pairs[v.pair_nbr[pi.nbr_begin + c0 + lane]];
-          srect[lane] = make_int4(qn.x0, qn.y0, qn.w, qn.h);
-          soff[lane] = v.patches[qn.patch].pool_offset;
-        }
+        stage_neighbours(v, pi, c0, cnt, srect, soff, lane);
         __syncwarp();
         for (int q = item.start + lane; q < end; q += 32) {
           const int qy = q / pi.w;
@@ -880,15 +906,7 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
           } else {
             b = v.bg[pi.bg_base + q];
           }
-          for (int k = 0; k < cnt; ++k) {
-            const int4 r = srect[k];
-            const int lx = gx - r.x, ly = gy - r.y;
-            if (lx < 0 || ly < 0 || lx >= r.z || ly >= r.w) continue;
-            const float2 c = v.cache[soff[k] + ly * r.z + lx];
-            b.x += c.x;
-            b.y += c.y;
-          }
-          v.bg[pi.bg_base + q] = b;
+          v.bg[pi.bg_base + q] = add_neighbours(v, b, gx, gy, cnt, srect, soff);
         }
       }
       continue;
@@ -1128,6 +1146,16 @@ static size_t smem_bytes_grad(int wpb) { return (size_t)wpb * kDerivRecF * sizeo
 
 constexpr int kWpb = 4;   // warps per block of the pixel kernels
 
+// The derivative kernel's dynamic shared memory is close to the default 48 KB
+// limit: raise the limit to what it uses.
+static DeviceOnce g_derivs_attr;
+static cudaError_t derivs_attr() {
+  return g_derivs_attr.run([] {
+    return cudaFuncSetAttribute(derivs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes_derivs(kWpb));
+  });
+}
+
 // Resident blocks per SM of each persistent pixel kernel, per device (0
 // until measured on that device).
 enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccCommit, kOccKinds };
@@ -1135,6 +1163,7 @@ static std::atomic<int> g_occ[kMaxDevices][kOccKinds] = {};
 static DeviceOnce g_occ_once;
 
 cudaError_t init_pixel_occupancy() {
+  if (cudaError_t e = derivs_attr()) return e;
   return g_occ_once.run([] {
     const int dev = current_device();
     const size_t sm = smem_bytes(kWpb);
@@ -1184,9 +1213,9 @@ cudaError_t launch_background(const Launch& L, const PlanView& v) {
 
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
+  if (cudaError_t e = derivs_attr()) return e;
   derivs_kernel<<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32, smem_bytes_derivs(kWpb),
-                  L.stream>>>(
-      v, L.n_exp, L.n_dev);
+                  L.stream>>>(v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
