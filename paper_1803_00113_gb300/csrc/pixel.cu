@@ -396,7 +396,15 @@ __device__ __forceinline__ void pixel_derivs(const float* __restrict__ rec, int 
     const float* base = rec + kCompBase + kPsf * kStarF + k * per * kGalF;
     const Offset o = make_offset(pixel_delta(rec, k, px, py));
     const Offset2 o2 = dup_offset(o);
-    for (int j = 0; j < nb; ++j) gal_accumulate2(base + j * 2 * kGalF, o2, g2);
+    if (nb == kMaxProf) {
+      // the usual eight pairs, unrolled: independent pairs interleave (the
+      // loop over PSF components stays rolled: unrolling both measured
+      // slower, from instruction fetch)
+#pragma unroll
+      for (int j = 0; j < kMaxProf; ++j) gal_accumulate2(base + j * 2 * kGalF, o2, g2);
+    } else {
+      for (int j = 0; j < nb; ++j) gal_accumulate2(base + j * 2 * kGalF, o2, g2);
+    }
     const float* single = base + nb * 2 * kGalF;
     for (int j = nb; j < ne; ++j, single += kGalF) gal_single<0>(single, o, g2);
     for (int j = nb; j < nd; ++j, single += kGalF) gal_single<1>(single, o, g2);
