@@ -600,6 +600,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and world == 1:
         serving = serving_summary(cel, args, local)
+    differentiation = None
+    if args.workload == "batched" and not args.no_field:
+        differentiation = differentiation_summary(cel, dev, local)
 
     # ---- roofline of the derivative pixel kernel
     props = torch.cuda.get_device_properties(dev)
@@ -660,6 +663,8 @@ def run_ours(args):
         line["single_field"] = extra_field
     if serving:
         line["serving"] = serving
+    if differentiation:
+        line["differentiation"] = differentiation
     if not args.no_cpu_baseline and world == 1:
         rng = np.random.default_rng(0)
         order = list(rng.permutation(problem.n_sources))
@@ -804,6 +809,47 @@ def _serve_run(cel, srv, pool, arrivals):
         out.append(r)
     wall = time.perf_counter() - t0
     return out, wall
+
+
+def differentiation_summary(cel, dev, local, reps=10):
+    """Config 4: the autograd function over the hand-written adjoint on 1,024
+    sources of the field generator (all in one plan): value + gradient via
+    backward, and Hessian-vector products via double backward, event-timed."""
+    import torch
+    from paper_1803_00113_gb300.autograd import SourceObjective
+    p = fields.single_field(seed=SEED + 4, n_sources=1024)
+    ctx = cel.Context(p.model, device=local)
+    dp = cel.DeviceProblem(p, dev)
+    plan = cel.Plan(ctx, dp, list(range(p.n_sources)))
+    obj = SourceObjective(plan)
+    theta0 = torch.tensor(p.theta, dtype=torch.float64, device=dev)
+    v = torch.ones_like(theta0)
+
+    def grad_once():
+        t = theta0.clone().requires_grad_(True)
+        obj(t).sum().backward()
+        return t.grad
+
+    def hvp_once():
+        return torch.autograd.functional.hvp(lambda t: obj(t).sum(), theta0, v)[1]
+
+    out = {"workload": "1,024 sources of the single-field generator, one plan, neighbours "
+                       "frozen; patch-level recomputation (nothing stored per pixel)",
+           "visits_per_evaluation": plan.visits}
+    for name, fn in (("value_and_gradient", grad_once), ("hessian_vector_product", hvp_once)):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"ms": ms, "visits_per_s": plan.visits / (ms / 1e3)}
+    plan.close()
+    ctx.close()
+    return out
 
 
 def serving_summary(cel, args, local, rates=(200.0, 2000.0), seconds=2.0):
