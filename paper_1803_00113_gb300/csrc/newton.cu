@@ -634,6 +634,73 @@ __device__ void first_order(TrSmem& S, int lane, double dl) {
   __syncwarp();
 }
 
+// Warp 0: x = L^{-T} z (rows on lanes).
+__device__ __forceinline__ double back_sweep(const TrSmem& S, double z, int lane) {
+  for (int k = N - 1; k > 0; --k) {
+    const double xk = __shfl_sync(0xffffffffu, z, k);
+    if (lane < k) z = fma(-S.ws.f.L[k * N + lane], xk, z);
+  }
+  return z;
+}
+
+// Warp 0: x = (L D L^T)^{-1} b.
+__device__ __forceinline__ double full_solve(const TrSmem& S, double b, int lane) {
+  for (int k = 0; k < N - 1; ++k) {
+    const double bk = __shfl_sync(0xffffffffu, b, k);
+    if (lane > k && lane < N) b = fma(-S.ws.f.L[lane * N + k], bk, b);
+  }
+  return back_sweep(S, lane < N ? b * S.Dinv[lane] : 0.0, lane);
+}
+
+// Warp 0: the step at the multiplier l0 + d with |p(l0 + d)| = Delta, from
+// the factorisation at l0 alone.  With A = B + l0 I and w_k = A^{-k} p(l0),
+// p(l0 + d) = sum_k (-d)^k w_k (a Neumann series; four terms leave a
+// relative error of about (d / gap)^4, gap the distance of l0 from the
+// pole) and A(d)^{-1} p(l0 + d) = sum_n (n + 1) (-d)^n w_{n+1}; Newton's
+// iteration on 1/|p| - 1/Delta (Nocedal & Wright, Algorithm 4.3) then runs
+// on the scalars of the Gram matrix w_i . w_j.  On entry S.p = p(l0) and
+// S.z = L^{-1} p(l0) (from ldl_solve_full); d0 is the first Newton step.
+// On exit S.p is the step.
+__device__ void series_finish(TrSmem& S, int lane, double d0, double Delta) {
+  constexpr int K = 3;
+  double w[K + 1];
+  w[0] = lane < N ? S.p[lane] : 0.0;
+  w[1] = back_sweep(S, lane < N ? S.z[lane] * S.Dinv[lane] : 0.0, lane);
+#pragma unroll
+  for (int k = 2; k <= K; ++k) w[k] = full_solve(S, w[k - 1], lane);
+  double G[K + 1][K + 1];
+#pragma unroll
+  for (int i = 0; i <= K; ++i)
+#pragma unroll
+    for (int j = i; j <= K; ++j) G[i][j] = G[j][i] = warp_sum_d(w[i] * w[j]);
+  double d = d0;
+  double c[K + 1];
+  for (int it = 0; it < 8; ++it) {
+    c[0] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= K; ++k) c[k] = -d * c[k - 1];
+    double n2 = 0.0, q = 0.0;
+#pragma unroll
+    for (int i = 0; i <= K; ++i) {
+#pragma unroll
+      for (int j = 0; j <= K; ++j) n2 = fma(c[i] * c[j], G[i][j], n2);
+#pragma unroll
+      for (int n = 0; n < K; ++n) q = fma(c[i] * (double)(n + 1) * c[n], G[i][n + 1], q);
+    }
+    const double step = (sqrt(n2) - Delta) / Delta * n2 / q;
+    d += step;
+    if (!(fabs(step) > 1e-15 * fabs(d))) break;
+  }
+  c[0] = 1.0;
+#pragma unroll
+  for (int k = 1; k <= K; ++k) c[k] = -d * c[k - 1];
+  double x = 0.0;
+#pragma unroll
+  for (int k = K; k >= 0; --k) x = fma(c[k], w[k], x);
+  if (lane < N) S.p[lane] = x;
+  __syncwarp();
+}
+
 // Householder reduction of B (FP32, in S.ws.f.Bf) to tridiagonal form by all
 // four warps: thread t owns row t / 4 of the trailing block and, in it, the
 // columns c = t (mod 4); two block barriers per reflection.  Every warp
@@ -904,6 +971,11 @@ __device__ bool tr_solve(TrSmem& S, const double* __restrict__ g, const double* 
               const bool inside = ln > fmax(lo, 0.0) && (hi < 0.0 || ln < hi);
               if (inside && gap > 0.0 && fabs(dl) <= 1e-5 * gap) {
                 first_order(S, lane, dl);
+                fin = true;
+              } else if (inside && gap > 0.0 && fabs(dl) <= 1e-3 * gap) {
+                // still close: finish on this factorisation (a series in
+                // the multiplier) instead of factorising again
+                series_finish(S, lane, dl, Delta);
                 fin = true;
               } else if (inside) {
                 next = ln;
