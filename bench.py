@@ -326,6 +326,7 @@ class NewtonPass:
         self.delta0, self.status0 = self.delta.clone(), self.status.clone()
         self.render_all()
         self.cache0 = dp.cache.clone() if dp.cache is not None else None
+        self.half0 = dp.cache_half.clone() if dp.cache is not None else None
         self.graph = None
         # the library counts the kernels it launches: one eager step's worth
         self.reset()
@@ -354,6 +355,7 @@ class NewtonPass:
         self.status.copy_(self.status0)
         if self.cache0 is not None:
             self.dp.cache.copy_(self.cache0)
+            self.dp.cache_half.copy_(self.half0)
 
     def step_eager(self):
         for p in self.plans:

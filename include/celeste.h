@@ -145,10 +145,19 @@ typedef struct celeste_problem {
    * each of its patch pixels, in the patch-pool layout ([n_pool] pairs at
    * each patch's pool_offset).  With it, neighbour backgrounds are gathered
    * from the cache instead of re-rendering every neighbour (the same values,
-   * bit for bit).  celeste_newton_step re-renders the sources whose step
-   * was accepted and celeste_fit_run keeps it current; after changing theta
-   * any other way, refresh it with celeste_render_cache. */
+   * bit for bit).  celeste_newton_step keeps it current for the sources
+   * whose step was accepted and celeste_fit_run keeps it current; after
+   * changing theta any other way, refresh it with celeste_render_cache. */
   float* render_cache;
+  /* Optional (may be NULL; read only with render_cache): [n_sources] bytes,
+   * 0 or 1, on the device.  When given, render_cache holds two halves of
+   * n_pool float2 each (4 n_pool floats) and render_cache_half[s] names the
+   * half that holds source s's current moments (zeros: all in the first).
+   * celeste_newton_step then renders each trial point into the source's
+   * other half and flips the entry of the sources whose step it accepts,
+   * which moves no pixel data; without it the step copies the accepted
+   * renders into the single cache. */
+  uint8_t* render_cache_half;
 } celeste_problem;
 
 /* Tile shape of the pixel kernels: the number of pixels one warp reduces

@@ -22,7 +22,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(OUT_DIR, "libceleste.so")
-SOURCES = ["setup.cu", "pixel.cu", "epilogue.cu", "newton.cu", "fit.cu", "field.cu", "firstorder.cu", "serve.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "pixel.cu", "epilogue.cu", "newton.cu", "step.cu", "fit.cu", "field.cu",
+           "firstorder.cu", "serve.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          f"-I{INCLUDE}"]

@@ -74,7 +74,7 @@ class _Problem(ctypes.Structure):
         ("n_pixels", ctypes.c_int64), ("n_sky", ctypes.c_int64), ("n_pool", ctypes.c_int64),
         ("n_images", ctypes.c_int32), ("n_sources", ctypes.c_int32),
         ("n_patches", ctypes.c_int32), ("n_nbr", ctypes.c_int32),
-        ("render_cache", ctypes.c_void_p)]
+        ("render_cache", ctypes.c_void_p), ("render_cache_half", ctypes.c_void_p)]
 
 
 class _Tuning(ctypes.Structure):
@@ -358,10 +358,15 @@ class DeviceProblem:
         s.n_pixels, s.n_sky, s.n_pool = p.pixels.size, p.sky.size, self.n_pool
         s.n_images, s.n_sources, s.n_patches = p.n_images, p.n_sources, p.n_patches
         s.n_nbr = int(p.nbr_idx.size)
-        # (E, V) of every source at each of its patch pixels, pool layout
-        self.cache = (torch.zeros(2 * max(self.n_pool, 1), dtype=torch.float32, device=dev)
+        # (E, V) of every source at each of its patch pixels, pool layout, in
+        # two halves; cache_half[s] names the half with source s's current
+        # moments (a Newton step renders trial points into the other half)
+        self.cache = (torch.zeros(4 * max(self.n_pool, 1), dtype=torch.float32, device=dev)
                       if render_cache else None)
+        self.cache_half = (torch.zeros(max(p.n_sources, 1), dtype=torch.uint8, device=dev)
+                           if render_cache else None)
         s.render_cache = self.cache.data_ptr() if render_cache else None
+        s.render_cache_half = self.cache_half.data_ptr() if render_cache else None
         self.struct = s
 
     @property

@@ -283,20 +283,17 @@ bool prepare_model(const celeste_model* m, ModelDev* md) {
 }  // namespace celeste
 
 // One trust-region Newton iteration of the plan's active sources once the
-// neighbour records and background are in place: own records, derivative
-// pass, epilogue, FP64 step, trial records, trial value, accept.
+// neighbour records and background are in place: active set and own
+// records, derivative pass, the per-source step (epilogue, trust-region
+// step, trial records), the value pass at the trial points, accept rule.
 cudaError_t celeste::enqueue_iteration(celeste_ctx* c, celeste_plan* p, const Launch& L,
                                      double* delta, int32_t* status) {
   PlanView& v = p->v;
-  cudaError_t e = launch_mark_active(L, v, status);
-  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, false);
+  cudaError_t e = launch_prepare(L, v, c->d_model, status, v.n_own_pairs, false);
   if (e == cudaSuccess) e = launch_pixels_derivs(L, v);
-  if (e == cudaSuccess) e = launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
-  if (e == cudaSuccess) e = launch_tr_step(L, v, delta, status);
-  if (e == cudaSuccess) e = launch_setup(L, v, c->d_model, 0, v.n_own_pairs, true);
-  if (e == cudaSuccess) e = launch_pixels_value(L, v);
-  if (e == cudaSuccess) e = launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
-  if (e == cudaSuccess) e = launch_tr_accept(L, v, p->rel_trial, delta, status);
+  if (e == cudaSuccess) e = launch_source_step(L, v, c->d_model, delta, status);
+  if (e == cudaSuccess) e = launch_pixels_value(L, v, false);
+  if (e == cudaSuccess) e = launch_slot_finish(L, v, false, delta, status);
   return e;
 }
 
@@ -424,7 +421,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
     seen[ids[j]] = 1;
   }
   std::vector<PairInfo> pairs;
-  std::vector<int32_t> slot_ptr(n + 1, 0), pair_nbr;
+  std::vector<int32_t> slot_ptr(n + 1, 0), slot_items(n + 1, 0), pair_nbr;
   std::vector<Item> items;
   int64_t bg = 0, visits = 0;
   auto patch_ok = [&](const celeste_patch& q) {
@@ -465,6 +462,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
       pairs.push_back(pi);
     }
     slot_ptr[j + 1] = (int)pairs.size();
+    slot_items[j + 1] = (int)items.size();
   }
   const int n_own = (int)pairs.size();
   // neighbour pairs: (neighbour source, its patch in the same image) that
@@ -547,12 +545,15 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   v.n_bg = bg;
   v.err = c->d_err;
   v.cache = reinterpret_cast<float2*>(pr->render_cache);
+  v.cache_half = pr->render_cache ? pr->render_cache_half : nullptr;
+  v.cache_n_pool = pr->n_pool;
   v.patches = pr->patches;
   p->d_patches = pr->patches;
   int32_t* d_ids = dev_alloc<int32_t>(p, n, &err);
   PairInfo* d_pairs = dev_alloc<PairInfo>(p, pairs.size(), &err);
   int32_t* d_nbr = dev_alloc<int32_t>(p, pair_nbr.size(), &err);
   int32_t* d_slot = dev_alloc<int32_t>(p, n + 1, &err);
+  int32_t* d_slot_items = dev_alloc<int32_t>(p, n + 1, &err);
   Item* d_items = dev_alloc<Item>(p, items.size(), &err);
   v.records = dev_alloc<float>(p, pairs.size() * (size_t)kRecF, &err);
   v.bg = dev_alloc<float2>(p, (size_t)bg, &err);
@@ -562,8 +563,10 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   v.theta_trial = dev_alloc<double>(p, (size_t)n * kTheta, &err);
   v.step = dev_alloc<double>(p, (size_t)n * kTheta, &err);
   v.pred = dev_alloc<double>(p, n, &err);
+  v.kl_trial = dev_alloc<double>(p, n, &err);
   v.elbo_rel = dev_alloc<double>(p, n, &err);
   p->rel_trial = dev_alloc<double>(p, n, &err);
+  v.rel_trial = p->rel_trial;
   v.grad = dev_alloc<double>(p, (size_t)n * kTheta, &err);
   v.hess = dev_alloc<double>(p, (size_t)n * kTheta * kTheta, &err);
   v.active = dev_alloc<uint8_t>(p, n, &err);
@@ -579,6 +582,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   cp(d_pairs, pairs.data(), pairs.size() * sizeof(PairInfo));
   cp(d_nbr, pair_nbr.data(), pair_nbr.size() * sizeof(int32_t));
   cp(d_slot, slot_ptr.data(), (n + 1) * sizeof(int32_t));
+  cp(d_slot_items, slot_items.data(), (n + 1) * sizeof(int32_t));
   cp(d_items, items.data(), items.size() * sizeof(Item));
   if (ce == cudaSuccess) ce = cudaMemset(v.theta_trial, 0, (size_t)n * kTheta * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMemset(v.active, 1, n > 0 ? n : 1);
@@ -590,6 +594,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   v.pairs = d_pairs;
   v.pair_nbr = d_nbr;
   v.slot_pair_ptr = d_slot;
+  v.slot_items = d_slot_items;
   v.items = d_items;
   *out = p;
   return CELESTE_OK;
@@ -683,33 +688,32 @@ int celeste_newton_step(celeste_ctx* c, const celeste_plan* pc, double* delta, i
   if (p->v.n == 0) return CELESTE_OK;
   Launch L = make_launch(c, p);
   PlanView& v = p->v;
+  const bool cached = v.cache != nullptr;
+  // active set and records; with a render cache the background comes from
+  // cached moments, so the own records are all it needs and it joins the
+  // same launch
   c->launches += 1;
-  CK(timed(c, CELESTE_K_OTHER, 0, L.stream, [&] { return launch_mark_active(L, v, status); }));
-  // with a render cache the background comes from cached moments, so only
-  // the own pairs need records
-  int rc = run_setup(c, p, 0, v.cache ? v.n_own_pairs : v.n_pairs, false);
-  if (rc) return rc;
-  c->launches += 3;
-  CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, v); }));
+  CK(timed(c, cached ? CELESTE_K_BACKGROUND : CELESTE_K_SETUP, cached ? p->visits : 0, L.stream,
+           [&] {
+             return launch_prepare(L, v, c->d_model, status, cached ? v.n_own_pairs : v.n_pairs,
+                                   cached);
+           }));
+  if (!cached) {
+    c->launches += 1;
+    CK(timed(c, CELESTE_K_BACKGROUND, p->visits, L.stream, [&] { return launch_background(L, v); }));
+  }
+  c->launches += 2;
   CK(derivs_launch(c, p, L));
-  CK(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
-    return launch_epilogue(L, v, c->d_model, nullptr, v.elbo_rel, v.grad, v.hess);
-  }));
+  CK(timed(c, CELESTE_K_TRSTEP, 0, L.stream,
+           [&] { return launch_source_step(L, v, c->d_model, delta, status); }));
   if (elbo_rel) CK(cudaMemcpyAsync(elbo_rel, v.elbo_rel, v.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  c->launches += 1;
-  CK(timed(c, CELESTE_K_TRSTEP, 0, L.stream, [&] { return launch_tr_step(L, v, delta, status); }));
-  rc = run_setup(c, p, 0, v.n_own_pairs, true);
-  if (rc) return rc;
-  c->launches += 3;
+  c->launches += 2;
   CK(timed(c, CELESTE_K_VALUE, p->visits, L.stream,
            [&] { return launch_pixels_value(L, v, true); }));
-  CK(timed(c, CELESTE_K_EPILOGUE, 0, L.stream, [&] {
-    return launch_epilogue_value(L, v, c->d_model, nullptr, p->rel_trial, true);
-  }));
   CK(timed(c, CELESTE_K_OTHER, 0, L.stream,
-           [&] { return launch_tr_accept(L, v, p->rel_trial, delta, status); }));
-  if (v.cache) {
-    // accepted sources: their trial render becomes their cached render
+           [&] { return launch_slot_finish(L, v, true, delta, status); }));
+  if (cached && !v.cache_half) {
+    // one cache: accepted sources' trial renders are copied into it
     c->launches += 1;
     CK(timed(c, CELESTE_K_RENDER, p->visits, L.stream,
              [&] { return launch_commit_render(L, v, status); }));

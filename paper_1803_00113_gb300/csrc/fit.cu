@@ -313,11 +313,15 @@ int fit_build(celeste_fit* F) {
     celeste_plan* p = F->plans[k];
     Launch L = make_launch(c, p);
     L.stream = cs;
-    // neighbour records and background, once per class and pass
+    // neighbour records and background, once per class and pass (with a
+    // render cache the background needs no records: one launch)
     CK(begin());
-    e = launch_mark_active(L, p->v, f.status);
-    if (e == cudaSuccess) e = launch_setup(L, p->v, c->d_model, 0, p->v.n_pairs, false);
-    if (e == cudaSuccess) e = launch_background(L, p->v);
+    if (p->v.cache) {
+      e = launch_prepare(L, p->v, c->d_model, f.status, 0, true);
+    } else {
+      e = launch_prepare(L, p->v, c->d_model, f.status, p->v.n_pairs, false);
+      if (e == cudaSuccess) e = launch_background(L, p->v);
+    }
     e2 = end();
     CK(e);
     CK(e2);
@@ -425,9 +429,10 @@ int fit_pass_finish(celeste_ctx* c, celeste_fit* F, int* n_active) {
   *n_active = 0;
   if (f.n_region == 0) return CELESTE_OK;
   CK(cudaStreamSynchronize(c->stream));
-  // launches of the pass: reset and summary, per class 3 + the loop trips
+  // launches of the pass: reset and summary, per class 2 (with a render
+  // cache: 1, and 2 to refresh it at the end) + the loop trips
   int64_t nl = 2;
-  const int per_class = F->plans.empty() || !F->plans[0]->v.cache ? 3 : 5;
+  const int per_class = F->plans.empty() || !F->plans[0]->v.cache ? 2 : 3;
   for (int k = 0; k < f.n_classes; ++k)
     nl += per_class + (int64_t)F->h_summary[1 + k] * kIterationLaunches;
   c->launches += nl;

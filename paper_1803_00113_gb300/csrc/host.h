@@ -106,7 +106,7 @@ Launch make_launch(const celeste_ctx* c, const celeste_plan* p);
 // kernels; the fit adds its check kernel).
 cudaError_t enqueue_iteration(celeste_ctx* c, celeste_plan* p, const Launch& L, double* delta,
                               int32_t* status);
-constexpr int kIterationLaunches = 10;
+constexpr int kIterationLaunches = 6;
 
 // A fit over region sources cut into segments (independent requests):
 // ids[seg_ptr[k] .. seg_ptr[k+1]) is segment k; no source may have a

@@ -110,6 +110,7 @@ struct PlanView {
   const int32_t* pair_nbr;    // neighbour pair indices per own pair
   const int32_t* slot_pair_ptr;  // [n+1] own pairs per slot
   const Item* items;          // [n_items]
+  const int32_t* slot_items;  // [n+1] items of slot j: [slot_items[j], slot_items[j+1])
   float* records;             // [n_pairs][kRecF]
   float2* bg;                 // [n_bg] background (E, V) per own patch pixel
   float* partials;            // [n_items][kAcc]
@@ -117,12 +118,17 @@ struct PlanView {
   double* theta_trial;        // [n][27]
   double* step;               // [n][27]
   double* pred;               // [n]
+  double* kl_trial;           // [n] KL_s at theta_trial (the per-source Newton step)
+  double* rel_trial;          // [n] L_rel at theta_trial
   double* elbo_rel;           // [n] value at the current iterate
   double* grad;               // [n][27] scratch for newton_step
   double* hess;               // [n][27][27]
   uint8_t* active;            // [n] 1 if the slot takes part in the evaluation
   unsigned int* err;          // device error word
   float2* cache;              // problem render cache (pool layout) or null
+  uint8_t* cache_half;        // [n_sources] half of the cache holding each source's
+                              //     current moments (two halves of cache_n_pool), or null
+  int64_t cache_n_pool;       // float2 per half
   float2* trial_render;       // [n_bg] own moments at the trial point (with a cache)
   const celeste_patch* patches;  // problem patches (pool offsets)
   int32_t n, n_pairs, n_own_pairs, n_items;
@@ -149,8 +155,9 @@ cudaError_t init_pixel_occupancy();
 cudaError_t launch_background(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v);
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v);
-// keep_render: also store the own moments in v.trial_render (for a later
-// commit to the render cache of the sources whose step is accepted)
+// keep_render (with a render cache): also store the own moments, in the
+// source's other half of the cache when it has two (the accept rule then
+// flips the half), else in v.trial_render (for the commit kernel)
 cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render = false);
 cudaError_t launch_render(const Launch& L, const PlanView& v, float* E_out, float* V_out,
                           const celeste_patch* patches);
@@ -172,6 +179,11 @@ cudaError_t launch_field_sum(const Launch& L, const double* parts, int n_parts, 
                              int n_kl, double* out);
 // epilogue.cu: KL_s of each slot's source at theta into kl_out[source id].
 cudaError_t launch_kl(const Launch& L, const PlanView& v, const ModelDev* model, double* kl_out);
+// The start of a Newton iteration of a colour class in one launch: the
+// active set from status, the records of pairs [0, n_setup) at theta and,
+// with background (render cache only), the backgrounds of the active slots.
+cudaError_t launch_prepare(const Launch& L, const PlanView& v, const ModelDev* model,
+                           const int32_t* status, int n_setup, bool background);
 // Copies v.trial_render into the render cache for slots whose source's
 // status is CELESTE_ST_ACCEPTED.
 cudaError_t launch_commit_render(const Launch& L, const PlanView& v, const int32_t* status);
@@ -185,14 +197,19 @@ cudaError_t launch_epilogue_loglik(const Launch& L, const PlanView& v, const Mod
                                    double* out);
 cudaError_t launch_epilogue_value(const Launch& L, const PlanView& v, const ModelDev* model,
                                   double* elbo, double* elbo_rel, bool use_trial);
+// step.cu: the per-source part of a Newton iteration in one launch: the
+// epilogue at theta, the trust-region step, KL_s at theta_trial and the own
+// pairs' records at theta_trial.
+cudaError_t launch_source_step(const Launch& L, const PlanView& v, const ModelDev* model,
+                               double* delta, int32_t* status);
+// step.cu: the end of the iteration, after the value pass at theta_trial:
+// L_rel at theta_trial (into v.rel_trial), the accept rule and, with
+// flip_cache and two render-cache halves, the accepted sources' halves.
+cudaError_t launch_slot_finish(const Launch& L, const PlanView& v, bool flip_cache,
+                               double* delta, int32_t* status);
 // newton.cu
-cudaError_t launch_tr_step(const Launch& L, const PlanView& v, const double* delta,
-                           int32_t* status);
-cudaError_t launch_tr_accept(const Launch& L, const PlanView& v, const double* rel_trial,
-                             double* delta, int32_t* status);
 cudaError_t launch_tr_subproblem(const Launch& L, int n, const double* g, const double* H,
                                  const double* delta, double* p, double* pred);
-cudaError_t launch_mark_active(const Launch& L, const PlanView& v, const int32_t* status);
 
 // fit.cu: the region fit's per-source state (device arrays indexed by source
 // id unless noted) and its bookkeeping kernels.  The region is cut into
@@ -238,6 +255,17 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// A slot takes part in a Newton iteration unless its source has stopped.
+__device__ __forceinline__ uint8_t active_of(int32_t st) {
+  return (st == CELESTE_ST_CONVERGED || st == CELESTE_ST_FAILED || st == CELESTE_ST_MAXITER) ? 0
+                                                                                             : 1;
+}
+
+// Offset of source s's current half of the render cache.
+__device__ __forceinline__ int64_t cache_base(const PlanView& v, int s) {
+  return v.cache_half && v.cache_half[s] ? v.cache_n_pool : 0;
 }
 
 // Bilinear sky at pixel (x, y) of image `im` (knots span the image).

@@ -21,6 +21,7 @@
 
 #include "device_once.h"
 #include "internal.cuh"
+#include "setup.cuh"
 
 namespace celeste {
 
@@ -806,6 +807,43 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
   }
 }
 
+// Value-only pass over one item: the pixel term at the record's point
+// (relative and baseline sums into the item's slot of vpartials); with
+// render set, the own moments are also stored there (row-major over the
+// patch, item pixels only).
+__device__ __forceinline__ void value_item(const PlanView& v, int it, const Item& item,
+                                           const PairInfo& pi, float* rec, int lane, int ne,
+                                           int nd, float2* render) {
+  __syncwarp();
+  stage_record<false>(rec, v.records + (size_t)item.pair * kRecF, kPsf * (1 + ne + nd), lane, ne);
+  __syncwarp();
+  float rel = 0.f, base = 0.f;
+  const int end = item.start + item.count;
+  for (int q = item.start + lane; q < end; q += 32) {
+    const int qy = q / pi.w;
+    const int qx = q - qy * pi.w;
+    const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
+    const float2 bg = v.bg[pi.bg_base + q];
+    float F0, F1, Es, Vs;
+    profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
+    own_moments(rec, F0, F1, Es, Vs);
+    if (render) render[q] = make_float2(Es, Vs);
+    const float E = bg.x + Es, V = bg.y + Vs;
+    const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
+    rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
+    base += fmaf(x, __logf(bg.x) - 0.5f * bg.y * rb * rb, -bg.x);
+  }
+  rel = warp_sum(rel);
+  base = warp_sum(base);
+  if (lane == 0) {
+    v.vpartials[2 * (size_t)it] = rel;
+    v.vpartials[2 * (size_t)it + 1] = base;
+  }
+}
+
+// keep_render: 0 none; 1 the own moments into v.trial_render; 2 into the
+// source's other half of the render cache (where a Newton step's trial
+// render waits for the accept rule).
 __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
                                                     int keep_render) {
   extern __shared__ float4 smem4[];
@@ -818,43 +856,25 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
-    __syncwarp();
-    stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
-                        kPsf * (1 + ne + nd), lane, ne);
-    __syncwarp();
-    float rel = 0.f, base = 0.f;
-    const int end = item.start + item.count;
-    for (int q = item.start + lane; q < end; q += 32) {
-      const int qy = q / pi.w;
-      const int qx = q - qy * pi.w;
-      const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
-      const float2 bg = v.bg[pi.bg_base + q];
-      float F0, F1, Es, Vs;
-      profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
-      own_moments(rec, F0, F1, Es, Vs);
-      if (keep_render) v.trial_render[pi.bg_base + q] = make_float2(Es, Vs);
-      const float E = bg.x + Es, V = bg.y + Vs;
-      const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
-      rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
-      base += fmaf(x, __logf(bg.x) - 0.5f * bg.y * rb * rb, -bg.x);
+    float2* render = nullptr;
+    if (keep_render == 1) {
+      render = v.trial_render + pi.bg_base;
+    } else if (keep_render == 2) {
+      const int64_t other = cache_base(v, pi.source) ? 0 : v.cache_n_pool;
+      render = v.cache + other + v.patches[pi.patch].pool_offset;
     }
-    rel = warp_sum(rel);
-    base = warp_sum(base);
-    if (lane == 0) {
-      v.vpartials[2 * (size_t)it] = rel;
-      v.vpartials[2 * (size_t)it + 1] = base;
-    }
+    value_item(v, it, item, pi, rec, lane, ne, nd, render);
   }
 }
 
 // Stages neighbour pairs [c0, c0 + cnt) of own pair pi: rectangle and offset
-// of the neighbour's patch in the render cache.
+// of the neighbour's patch in the render cache (in its current half).
 __device__ __forceinline__ void stage_neighbours(const PlanView& v, const PairInfo& pi, int c0,
                                                  int cnt, int4* srect, int64_t* soff, int lane) {
   if (lane < cnt) {
     const PairInfo qn = v.pairs[v.pair_nbr[pi.nbr_begin + c0 + lane]];
     srect[lane] = make_int4(qn.x0, qn.y0, qn.w, qn.h);
-    soff[lane] = v.patches[qn.patch].pool_offset;
+    soff[lane] = v.patches[qn.patch].pool_offset + cache_base(v, qn.source);
   }
 }
 
@@ -874,8 +894,73 @@ __device__ __forceinline__ float2 add_neighbours(const PlanView& v, float2 b, in
   return b;
 }
 
-// Background of every own patch pixel: sky plus each neighbour's E and V
-// where the pixel lies in that neighbour's patch (support rule, Sec. 2.2.3).
+// Background of item it's pixels (own pair pi): sky plus each neighbour's E
+// and V where the pixel lies in that neighbour's patch (support rule, Sec.
+// 2.2.3).  rec: the warp's staging area (kValRecF floats).
+__device__ __forceinline__ void background_item(const PlanView& v, const Item& item,
+                                                const PairInfo& pi, float* rec, int lane, int ne,
+                                                int nd) {
+  const celeste_image& im = v.images[pi.image];
+  const int end = item.start + item.count;
+  if (v.cache) {
+    // sky plus the neighbours' cached moments (the values the render
+    // below would produce, added in the same order), 32 neighbour pairs
+    // at a time staged in the warp's shared memory; the first 32 are
+    // added in the pass that evaluates the sky
+    int4* srect = reinterpret_cast<int4*>(rec);
+    int64_t* soff = reinterpret_cast<int64_t*>(rec + 4 * 32);
+    const int nn = pi.nbr_end - pi.nbr_begin;
+    for (int c0 = 0; c0 == 0 || c0 < nn; c0 += 32) {
+      const int cnt = max(0, min(32, nn - c0));
+      __syncwarp();
+      stage_neighbours(v, pi, c0, cnt, srect, soff, lane);
+      __syncwarp();
+      for (int q = item.start + lane; q < end; q += 32) {
+        const int qy = q / pi.w;
+        const int qx = q - qy * pi.w;
+        const int gx = pi.x0 + qx, gy = pi.y0 + qy;
+        float2 b;
+        if (c0 == 0) {
+          const float s = sky_value(im, v.sky, (float)gx, (float)gy);
+          if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
+          b = make_float2(s, 0.f);
+        } else {
+          b = v.bg[pi.bg_base + q];
+        }
+        v.bg[pi.bg_base + q] = add_neighbours(v, b, gx, gy, cnt, srect, soff);
+      }
+    }
+    return;
+  }
+  for (int q = item.start + lane; q < end; q += 32) {
+    const int qy = q / pi.w;
+    const int qx = q - qy * pi.w;
+    const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
+    if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
+    v.bg[pi.bg_base + q] = make_float2(s, 0.f);
+  }
+  for (int nb = pi.nbr_begin; nb < pi.nbr_end; ++nb) {
+    const int np = v.pair_nbr[nb];
+    const PairInfo qn = v.pairs[np];
+    __syncwarp();
+    stage_record<false>(rec, v.records + (size_t)np * kRecF, kPsf * (1 + ne + nd), lane, ne);
+    __syncwarp();
+    for (int q = item.start + lane; q < end; q += 32) {
+      const int qy = q / pi.w;
+      const int gx = pi.x0 + (q - qy * pi.w), gy = pi.y0 + qy;
+      const int lx = gx - qn.x0, ly = gy - qn.y0;
+      if (lx < 0 || ly < 0 || lx >= qn.w || ly >= qn.h) continue;
+      float F0, F1, Es, Vs;
+      profiles_value(rec, ne, nd, (float)lx, (float)ly, F0, F1);
+      own_moments(rec, F0, F1, Es, Vs);
+      float2 b = v.bg[pi.bg_base + q];
+      b.x += Es;
+      b.y += Vs;
+      v.bg[pi.bg_base + q] = b;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -887,65 +972,37 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
-    const celeste_image& im = v.images[pi.image];
-    const int end = item.start + item.count;
-    if (v.cache) {
-      // sky plus the neighbours' cached moments (the values the render
-      // below would produce, added in the same order), 32 neighbour pairs
-      // at a time staged in the warp's shared memory; the first 32 are
-      // added in the pass that evaluates the sky
-      int4* srect = reinterpret_cast<int4*>(rec);
-      int64_t* soff = reinterpret_cast<int64_t*>(rec + 4 * 32);
-      const int nn = pi.nbr_end - pi.nbr_begin;
-      for (int c0 = 0; c0 == 0 || c0 < nn; c0 += 32) {
-        const int cnt = max(0, min(32, nn - c0));
-        __syncwarp();
-        stage_neighbours(v, pi, c0, cnt, srect, soff, lane);
-        __syncwarp();
-        for (int q = item.start + lane; q < end; q += 32) {
-          const int qy = q / pi.w;
-          const int qx = q - qy * pi.w;
-          const int gx = pi.x0 + qx, gy = pi.y0 + qy;
-          float2 b;
-          if (c0 == 0) {
-            const float s = sky_value(im, v.sky, (float)gx, (float)gy);
-            if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
-            b = make_float2(s, 0.f);
-          } else {
-            b = v.bg[pi.bg_base + q];
-          }
-          v.bg[pi.bg_base + q] = add_neighbours(v, b, gx, gy, cnt, srect, soff);
-        }
-      }
-      continue;
-    }
-    for (int q = item.start + lane; q < end; q += 32) {
-      const int qy = q / pi.w;
-      const int qx = q - qy * pi.w;
-      const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
-      if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
-      v.bg[pi.bg_base + q] = make_float2(s, 0.f);
-    }
-    for (int nb = pi.nbr_begin; nb < pi.nbr_end; ++nb) {
-      const int np = v.pair_nbr[nb];
-      const PairInfo qn = v.pairs[np];
-      __syncwarp();
-      stage_record<false>(rec, v.records + (size_t)np * kRecF,
-                          kPsf * (1 + ne + nd), lane, ne);
-      __syncwarp();
-      for (int q = item.start + lane; q < end; q += 32) {
-        const int qy = q / pi.w;
-        const int gx = pi.x0 + (q - qy * pi.w), gy = pi.y0 + qy;
-        const int lx = gx - qn.x0, ly = gy - qn.y0;
-        if (lx < 0 || ly < 0 || lx >= qn.w || ly >= qn.h) continue;
-        float F0, F1, Es, Vs;
-        profiles_value(rec, ne, nd, (float)lx, (float)ly, F0, F1);
-        own_moments(rec, F0, F1, Es, Vs);
-        float2 b = v.bg[pi.bg_base + q];
-        b.x += Es;
-        b.y += Vs;
-        v.bg[pi.bg_base + q] = b;
-      }
+    background_item(v, item, pi, rec, lane, ne, nd);
+  }
+}
+
+// The start of a Newton iteration of a colour class, one warp per unit of
+// work: the active set from the sources' status (a warp per 32 slots), the
+// records of pairs [0, n_setup) at theta, and, with bg set, the background
+// of every item of an active slot (the render cache supplies the
+// neighbours, so the own records are all it needs).
+__global__ void __launch_bounds__(128) prepare_kernel(PlanView v, const ModelDev* __restrict__ model,
+                                                      const int32_t* __restrict__ status,
+                                                      int n_setup, int bg, int ne, int nd) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* rec = smem + wib * kValRecF;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int n_mark = (v.n + 31) / 32;
+  const int units = n_mark + n_setup + (bg ? v.n_items : 0);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + wib; u < units; u += nwarps) {
+    if (u < n_mark) {
+      const int j = 32 * u + lane;
+      if (j < v.n) v.active[j] = active_of(status[v.src_ids[j]]);
+    } else if (u < n_mark + n_setup) {
+      setup_pair(v, model, u - n_mark, false, rec, rec + 32, lane);
+    } else {
+      const Item item = v.items[u - n_mark - n_setup];
+      const PairInfo pi = v.pairs[item.pair];
+      if (!active_of(status[pi.source])) continue;
+      background_item(v, item, pi, rec, lane, ne, nd);
     }
   }
 }
@@ -994,7 +1051,7 @@ __global__ void __launch_bounds__(128) render_cache_kernel(PlanView v, int ne, i
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (status && status[pi.source] != CELESTE_ST_ACCEPTED) continue;
-    float2* out = v.cache + v.patches[pi.patch].pool_offset;
+    float2* out = v.cache + cache_base(v, pi.source) + v.patches[pi.patch].pool_offset;
     __syncwarp();
     stage_record<false>(rec, v.records + (size_t)item.pair * kRecF,
                         kPsf * (1 + ne + nd), lane, ne);
@@ -1022,7 +1079,8 @@ __global__ void __launch_bounds__(128) commit_render_kernel(PlanView v,
     const PairInfo pi = v.pairs[item.pair];
     if (status[pi.source] != CELESTE_ST_ACCEPTED) continue;
     const float2* __restrict__ src = v.trial_render + pi.bg_base + item.start;
-    float2* __restrict__ dst = v.cache + v.patches[pi.patch].pool_offset + item.start;
+    float2* __restrict__ dst =
+        v.cache + cache_base(v, pi.source) + v.patches[pi.patch].pool_offset + item.start;
     const int n = item.count;
     for (int q0 = lane; q0 < n; q0 += 8 * 32) {
       float2 r[8];
@@ -1166,7 +1224,9 @@ static cudaError_t derivs_attr() {
 
 // Resident blocks per SM of each persistent pixel kernel, per device (0
 // until measured on that device).
-enum { kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccCommit, kOccKinds };
+enum {
+  kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccCommit, kOccPrepare, kOccKinds
+};
 static std::atomic<int> g_occ[kMaxDevices][kOccKinds] = {};
 static DeviceOnce g_occ_once;
 
@@ -1175,7 +1235,7 @@ cudaError_t init_pixel_occupancy() {
   return g_occ_once.run([] {
     const int dev = current_device();
     const size_t sm = smem_bytes(kWpb);
-    int occ[kOccKinds] = {0, 0, 0, 0, 0, 0};
+    int occ[kOccKinds] = {};
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccDerivs], derivs_kernel,
                                                                   kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
@@ -1192,6 +1252,9 @@ cudaError_t init_pixel_occupancy() {
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccCommit], commit_render_kernel,
                                                         kWpb * 32, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccPrepare], prepare_kernel,
+                                                        kWpb * 32, sm);
     if (e == cudaSuccess)
       for (int k = 0; k < kOccKinds; ++k) g_occ[dev][k].store(occ[k], std::memory_order_relaxed);
     return e;
@@ -1237,8 +1300,18 @@ cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
 
 cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render) {
   if (v.n_items == 0) return cudaSuccess;
+  const int mode = !keep_render || !v.cache ? 0 : (v.cache_half ? 2 : 1);
   value_kernel<<<grid_for(L, v.n_items, kWpb, kOccValue), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
-      v, L.n_exp, L.n_dev, keep_render && v.trial_render ? 1 : 0);
+      v, L.n_exp, L.n_dev, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const Launch& L, const PlanView& v, const ModelDev* model,
+                           const int32_t* status, int n_setup, bool background) {
+  const int units = (v.n + 31) / 32 + n_setup + (background ? v.n_items : 0);
+  if (units == 0) return cudaSuccess;
+  prepare_kernel<<<grid_for(L, units, kWpb, kOccPrepare), kWpb * 32, smem_bytes(kWpb),
+                   L.stream>>>(v, model, status, n_setup, background ? 1 : 0, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
