@@ -36,8 +36,8 @@ constexpr float kHalfLog2e = 0.72134752044448170368f;   // log2(e) / 2
 //   derivs layout: header | origins | star {A, lw | P, 0}
 //                                   | per PSF component k: galaxy pairs, then singles
 // A galaxy component has 16 values {A, lw | -P11, -P12, -P22, tau |
-// -2 P12, -2 P11^2, -2 P22^2, -2 P12^2 | -4 P12, 0, 0, 0}: the signs are
-// chosen so that no formula below negates an operand.  The components of PSF
+// -2 P12, -2 P11^2, -2 P22^2, -2 P12^2 | -4 P12, -2 P12 P11, -2 P12 P22, 0}:
+// the signs are chosen so that no formula below negates an operand.  The components of PSF
 // component k come in pairs (exponential j, de Vaucouleurs j) for
 // j < min(n_exp, n_dev), their values interleaved (exponential in the even
 // slots), so that one packed two-wide FP32 instruction (ffma2, which rounds
@@ -117,7 +117,7 @@ __device__ __forceinline__ void stage_record(float* __restrict__ dst, const floa
       const int j = dev ? jj - ne : jj;
       const float vals[kGalF] = {q.x, q.y, q.z, q.w, -p11, -p12, -p22, b.z,
                                  -2.f * p12, -2.f * p11 * p11, -2.f * p22 * p22, -2.f * p12 * p12,
-                                 -4.f * p12, 0.f, 0.f, 0.f};
+                                 -4.f * p12, (-2.f * p12) * p11, (-2.f * p12) * p22, 0.f};
       float* base = dst + kCompBase + kPsf * kStarF + k * per * kGalF;
       if (j < nb) {
         float* o = base + j * 2 * kGalF + (dev ? 1 : 0);
@@ -146,6 +146,27 @@ __device__ __forceinline__ float2 pixel_delta(const float* __restrict__ rec, int
 __device__ __forceinline__ Offset make_offset(float2 d) {
   return Offset{d.x, d.y, d.x * d.x, d.x * d.y, d.y * d.y};
 }
+// A lane's pixels q0, q0 + 32, q0 + 64, ... of a row-major patch of width w
+// as (column, row), without a division per pixel: a step of 32 pixels is
+// ay rows and ax columns, plus one row when the column passes w.
+struct PixelWalk {
+  int qx, qy, ax, ay;
+  __device__ __forceinline__ PixelWalk(int q0, int w) {
+    qy = q0 / w;
+    qx = q0 - qy * w;
+    ay = 32 / w;
+    ax = 32 - ay * w;
+  }
+  __device__ __forceinline__ void next(int w) {
+    qx += ax;
+    qy += ay;
+    if (qx >= w) {
+      qx -= w;
+      ++qy;
+    }
+  }
+};
+
 // Density (weight and normaliser included) of a component with coefficients q.
 __device__ __forceinline__ float gauss_density(const float4 q, const Offset& o) {
   return exp2f(fmaf(q.x, o.xx, fmaf(q.y, o.xy, fmaf(q.z, o.yy, q.w))));
@@ -170,7 +191,8 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, cons
   const float4 q = *reinterpret_cast<const float4*>(c);
   const float4 pp = *reinterpret_cast<const float4*>(c + 4);
   const float4 hc = *reinterpret_cast<const float4*>(c + 8);
-  const float m4P12 = c[12];
+  const float4 hd = *reinterpret_cast<const float4*>(c + 12);
+  const float m4P12 = hd.x, c4b = hd.y, c4d = hd.z;
   const float nP11 = pp.x, nP12 = pp.y, nP22 = pp.z, tau = pp.w, m2P12 = hc.x;
   const float z1 = fmaf(nP11, o.dx, nP12 * o.dy);       // -y1
   const float z2 = fmaf(nP12, o.dx, nP22 * o.dy);       // -y2
@@ -196,12 +218,12 @@ __device__ __forceinline__ void gal_accumulate(const float* __restrict__ c, cons
   g.t3b = fmaf(pz2, h11, fmaf(m2P12, pz1, g.t3b));
   g.t3c = fmaf(pz1, h22, fmaf(m2P12, pz2, g.t3c));
   g.t3d = fmaf(pz2, a2, g.t3d);
-  // fourth order, written with h = y y^T - P
-  const float y11 = z1 * z1, y22 = z2 * z2;
+  // fourth order, written with h = y y^T - P (y1^2 = h11 + P11, y2^2 =
+  // h22 + P22: the -2 P12 P terms are staged)
   g.t4a = fmaf(pt2, fmaf(h11, fmaf(4.f, nP11, h11), hc.y), g.t4a);
-  g.t4b = fmaf(pt2, fmaf(h12, a1, m2P12 * y11), g.t4b);
+  g.t4b = fmaf(pt2, fmaf(h12, a1, fmaf(m2P12, h11, c4b)), g.t4b);
   g.t4c = fmaf(pt2, fmaf(h11, h22, fmaf(h12, m4P12, hc.w)), g.t4c);
-  g.t4d = fmaf(pt2, fmaf(h12, a2, m2P12 * y22), g.t4d);
+  g.t4d = fmaf(pt2, fmaf(h12, a2, fmaf(m2P12, h22, c4d)), g.t4d);
   g.t4e = fmaf(pt2, fmaf(h22, fmaf(4.f, nP22, h22), hc.z), g.t4e);
 }
 
@@ -238,7 +260,9 @@ __device__ __forceinline__ void gal_accumulate2(const float* __restrict__ c, con
   const float4 pb = *reinterpret_cast<const float4*>(c + 12);
   const float4 ha = *reinterpret_cast<const float4*>(c + 16);
   const float4 hb = *reinterpret_cast<const float4*>(c + 20);
-  const float2 m4P12 = *reinterpret_cast<const float2*>(c + 24);
+  const float4 hq = *reinterpret_cast<const float4*>(c + 24);
+  const float2 c4d = *reinterpret_cast<const float2*>(c + 28);
+  const float2 m4P12 = make_float2(hq.x, hq.y), c4b = make_float2(hq.z, hq.w);
   const float2 A11 = make_float2(qa.x, qa.y), A12 = make_float2(qa.z, qa.w);
   const float2 A22 = make_float2(qb.x, qb.y), lw = make_float2(qb.z, qb.w);
   const float2 nP11 = make_float2(pa.x, pa.y), nP12 = make_float2(pa.z, pa.w);
@@ -270,11 +294,10 @@ __device__ __forceinline__ void gal_accumulate2(const float* __restrict__ c, con
   g.t3b = fma2(pz2, h11, fma2(m2P12, pz1, g.t3b));
   g.t3c = fma2(pz1, h22, fma2(m2P12, pz2, g.t3c));
   g.t3d = fma2(pz2, a2, g.t3d);
-  const float2 y11 = mul2(z1, z1), y22 = mul2(z2, z2);
   g.t4a = fma2(pt2, fma2(h11, fma2(four, nP11, h11), c4a), g.t4a);
-  g.t4b = fma2(pt2, fma2(h12, a1, mul2(m2P12, y11)), g.t4b);
+  g.t4b = fma2(pt2, fma2(h12, a1, fma2(m2P12, h11, c4b)), g.t4b);
   g.t4c = fma2(pt2, fma2(h11, h22, fma2(h12, m4P12, c4c)), g.t4c);
-  g.t4d = fma2(pt2, fma2(h12, a2, mul2(m2P12, y22)), g.t4d);
+  g.t4d = fma2(pt2, fma2(h12, a2, fma2(m2P12, h22, c4d)), g.t4d);
   g.t4e = fma2(pt2, fma2(h22, fma2(four, nP22, h22), c4e), g.t4e);
 }
 
@@ -760,9 +783,9 @@ __global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int 
 #pragma unroll
     for (int a = 0; a < kGradAcc; ++a) acc[a] = 0.f;
     const int end = item.start + item.count;
-    for (int q = item.start + lane; q < end; q += 32) {
-      const int qy = q / pi.w;
-      const int qx = q - qy * pi.w;
+    PixelWalk pw(item.start + lane, pi.w);
+    for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
+      const int qy = pw.qy, qx = pw.qx;
       const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
       const float2 bg = v.bg[pi.bg_base + q];
       pixel_derivs(rec, ne, nd, (float)qx, (float)qy, x, bg, acc, hs);
@@ -791,9 +814,9 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
 #pragma unroll
     for (int a = 0; a < kGradAcc; ++a) acc[a] = 0.f;
     const int end = item.start + item.count;
-    for (int q = item.start + lane; q < end; q += 32) {
-      const int qy = q / pi.w;
-      const int qx = q - qy * pi.w;
+    PixelWalk pw(item.start + lane, pi.w);
+    for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
+      const int qy = pw.qy, qx = pw.qx;
       const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
       const float2 bg = v.bg[pi.bg_base + q];
       pixel_grad(rec, ne, nd, (float)qx, (float)qy, x, bg, acc);
@@ -819,9 +842,9 @@ __device__ __forceinline__ void value_item(const PlanView& v, int it, const Item
   __syncwarp();
   float rel = 0.f, base = 0.f;
   const int end = item.start + item.count;
-  for (int q = item.start + lane; q < end; q += 32) {
-    const int qy = q / pi.w;
-    const int qx = q - qy * pi.w;
+  PixelWalk pw(item.start + lane, pi.w);
+  for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
+    const int qy = pw.qy, qx = pw.qx;
     const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
     const float2 bg = v.bg[pi.bg_base + q];
     float F0, F1, Es, Vs;
@@ -915,10 +938,9 @@ __device__ __forceinline__ void background_item(const PlanView& v, const Item& i
       __syncwarp();
       stage_neighbours(v, pi, c0, cnt, srect, soff, lane);
       __syncwarp();
-      for (int q = item.start + lane; q < end; q += 32) {
-        const int qy = q / pi.w;
-        const int qx = q - qy * pi.w;
-        const int gx = pi.x0 + qx, gy = pi.y0 + qy;
+      PixelWalk pw(item.start + lane, pi.w);
+      for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
+        const int gx = pi.x0 + pw.qx, gy = pi.y0 + pw.qy;
         float2 b;
         if (c0 == 0) {
           const float s = sky_value(im, v.sky, (float)gx, (float)gy);
@@ -932,10 +954,9 @@ __device__ __forceinline__ void background_item(const PlanView& v, const Item& i
     }
     return;
   }
-  for (int q = item.start + lane; q < end; q += 32) {
-    const int qy = q / pi.w;
-    const int qx = q - qy * pi.w;
-    const float s = sky_value(im, v.sky, (float)(pi.x0 + qx), (float)(pi.y0 + qy));
+  PixelWalk pw(item.start + lane, pi.w);
+  for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
+    const float s = sky_value(im, v.sky, (float)(pi.x0 + pw.qx), (float)(pi.y0 + pw.qy));
     if (!(s > 0.f)) set_error(v.err, CELESTE_DERR_SKY);
     v.bg[pi.bg_base + q] = make_float2(s, 0.f);
   }
