@@ -27,7 +27,9 @@ union StepSmem {
 };
 static_assert(sizeof(EpiSmem::Hnu) >= 3 * 64 * sizeof(float), "setup scratch of warps 1..3");
 
-__global__ void __launch_bounds__(kTrThreads, 4) source_step_kernel(PlanView v,
+// Five blocks per SM (96 registers, a few hundred bytes of spills): a colour
+// class of up to 760 sources runs in one round of blocks rather than two.
+__global__ void __launch_bounds__(kTrThreads, 5) source_step_kernel(PlanView v,
                                                                     const ModelDev* __restrict__ model,
                                                                     double* delta, int32_t* status) {
   extern __shared__ double smd[];
