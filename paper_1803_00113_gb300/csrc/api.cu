@@ -564,6 +564,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   v.step = dev_alloc<double>(p, (size_t)n * kTheta, &err);
   v.pred = dev_alloc<double>(p, n, &err);
   v.kl_trial = dev_alloc<double>(p, n, &err);
+  v.work_ctr = dev_alloc<int32_t>(p, 2, &err);
   v.elbo_rel = dev_alloc<double>(p, n, &err);
   p->rel_trial = dev_alloc<double>(p, n, &err);
   v.rel_trial = p->rel_trial;
@@ -586,6 +587,7 @@ int celeste_plan_create(celeste_ctx* c, const celeste_problem* pr, const int32_t
   cp(d_items, items.data(), items.size() * sizeof(Item));
   if (ce == cudaSuccess) ce = cudaMemset(v.theta_trial, 0, (size_t)n * kTheta * sizeof(double));
   if (ce == cudaSuccess) ce = cudaMemset(v.active, 1, n > 0 ? n : 1);
+  if (ce == cudaSuccess) ce = cudaMemset(v.work_ctr, 0, 2 * sizeof(int32_t));
   if (ce != cudaSuccess) {
     celeste_plan_destroy(p);
     return CELESTE_ECUDA;

@@ -118,6 +118,8 @@ struct PlanView {
   double* theta_trial;        // [n][27]
   double* step;               // [n][27]
   double* pred;               // [n]
+  int32_t* work_ctr;          // [2] work queue of the pixel kernels (next unit, warps done;
+                              //     zero between launches), or null for grid stride
   double* kl_trial;           // [n] KL_s at theta_trial (the per-source Newton step)
   double* rel_trial;          // [n] L_rel at theta_trial
   double* elbo_rel;           // [n] value at the current iterate

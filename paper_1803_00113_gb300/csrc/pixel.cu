@@ -146,6 +146,38 @@ __device__ __forceinline__ float2 pixel_delta(const float* __restrict__ rec, int
 __device__ __forceinline__ Offset make_offset(float2 d) {
   return Offset{d.x, d.y, d.x * d.x, d.x * d.y, d.y * d.y};
 }
+// Work units of a launch for one warp.  Warp w starts with unit w; with a
+// queue q ([0]: units handed out beyond the first per warp, [1]: warps done;
+// zero between launches) a warp then takes the next free unit whenever it
+// finishes one, asking for it while it works on the current one, so every
+// warp stays busy until the last unit; the last warp of the launch to finish
+// resets the queue.  Without one (q null) units are dealt out by grid
+// stride.  Every warp of the launch must reach done().
+struct WarpQueue {
+  int32_t* q;
+  int it, next, stride;
+  __device__ __forceinline__ WarpQueue(int32_t* queue) : q(queue), next(0) {
+    stride = gridDim.x * (blockDim.x >> 5);
+    it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  }
+  // at the top of every unit, before any continue
+  __device__ __forceinline__ void ask(int lane) {
+    if (q && lane == 0) next = stride + atomicAdd(q, 1);
+  }
+  __device__ __forceinline__ void advance() {
+    it = q ? __shfl_sync(0xffffffffu, next, 0) : it + stride;
+  }
+  __device__ __forceinline__ void done(int lane) {
+    if (q && lane == 0) {
+      __threadfence();
+      if (atomicAdd(q + 1, 1) == stride - 1) {
+        q[0] = 0;
+        q[1] = 0;
+      }
+    }
+  }
+};
+
 // A lane's pixels q0, q0 + 32, q0 + 64, ... of a row-major patch of width w
 // as (column, row), without a division per pixel: a step of 32 pixels is
 // ay rows and ax columns, plus one row when the column passes w.
@@ -760,6 +792,7 @@ __device__ __forceinline__ void reduce_tile(float* __restrict__ tile, float* __r
 // fed.  (Forming the background here instead of in background_kernel was
 // measured slower: the cached-moment loads inside the pixel loop stall 16
 // warps more than a separate kernel's many warps.)
+template <bool kQueue>
 __global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -768,8 +801,10 @@ __global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int 
   float* rec = smem + wib * kDerivWarpF;
   float* tile = rec + kDerivRecF;
   const HessAcc hs{tile + lane};
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+  WarpQueue wq(kQueue ? v.work_ctr : nullptr);
+  for (; wq.it < v.n_items; wq.advance()) {
+    wq.ask(lane);
+    const int it = wq.it;
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
@@ -793,16 +828,20 @@ __global__ void __launch_bounds__(128, 4) derivs_kernel(PlanView v, int ne, int 
     __syncwarp();
     reduce_tile(tile, acc, v.partials + (size_t)it * kAcc, lane);
   }
+  wq.done(lane);
 }
 
+template <bool kQueue>
 __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rec = smem + wib * kDerivRecF;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+  WarpQueue wq(kQueue ? v.work_ctr : nullptr);
+  for (; wq.it < v.n_items; wq.advance()) {
+    wq.ask(lane);
+    const int it = wq.it;
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
@@ -828,6 +867,7 @@ __global__ void __launch_bounds__(128) grad_kernel(PlanView v, int ne, int nd) {
     for (int a = 0; a < kGradAcc; ++a)
       if (a == lane) out[a] = acc[a];
   }
+  wq.done(lane);
 }
 
 // Value-only pass over one item: the pixel term at the record's point
@@ -867,6 +907,7 @@ __device__ __forceinline__ void value_item(const PlanView& v, int it, const Item
 // keep_render: 0 none; 1 the own moments into v.trial_render; 2 into the
 // source's other half of the render cache (where a Newton step's trial
 // render waits for the accept rule).
+template <bool kQueue>
 __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
                                                     int keep_render) {
   extern __shared__ float4 smem4[];
@@ -874,8 +915,10 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rec = smem + wib * kValRecF;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
+  WarpQueue wq(kQueue ? v.work_ctr : nullptr);
+  for (; wq.it < v.n_items; wq.advance()) {
+    wq.ask(lane);
+    const int it = wq.it;
     const Item item = v.items[it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
@@ -888,6 +931,7 @@ __global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
     }
     value_item(v, it, item, pi, rec, lane, ne, nd, render);
   }
+  wq.done(lane);
 }
 
 // Stages neighbour pairs [c0, c0 + cnt) of own pair pi: rectangle and offset
@@ -988,13 +1032,15 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rec = smem + wib * kValRecF;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < v.n_items; it += nwarps) {
-    const Item item = v.items[it];
+  WarpQueue wq(nullptr);   // grid stride: measured faster for the gather
+  for (; wq.it < v.n_items; wq.advance()) {
+    wq.ask(lane);
+    const Item item = v.items[wq.it];
     const PairInfo pi = v.pairs[item.pair];
     if (!v.active[pi.slot]) continue;
     background_item(v, item, pi, rec, lane, ne, nd);
   }
+  wq.done(lane);
 }
 
 // The start of a Newton iteration of a colour class, one warp per unit of
@@ -1010,10 +1056,12 @@ __global__ void __launch_bounds__(128) prepare_kernel(PlanView v, const ModelDev
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rec = smem + wib * kValRecF;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int n_mark = (v.n + 31) / 32;
   const int units = n_mark + n_setup + (bg ? v.n_items : 0);
-  for (int u = blockIdx.x * (blockDim.x >> 5) + wib; u < units; u += nwarps) {
+  WarpQueue wq(nullptr);   // grid stride: measured faster for the gather
+  for (; wq.it < units; wq.advance()) {
+    wq.ask(lane);
+    const int u = wq.it;
     if (u < n_mark) {
       const int j = 32 * u + lane;
       if (j < v.n) v.active[j] = active_of(status[v.src_ids[j]]);
@@ -1026,6 +1074,7 @@ __global__ void __launch_bounds__(128) prepare_kernel(PlanView v, const ModelDev
       background_item(v, item, pi, rec, lane, ne, nd);
     }
   }
+  wq.done(lane);
 }
 
 // Own E_s and V_s of every plan pair, scattered to the caller's pool layout.
@@ -1238,15 +1287,21 @@ constexpr int kWpb = 4;   // warps per block of the pixel kernels
 static DeviceOnce g_derivs_attr;
 static cudaError_t derivs_attr() {
   return g_derivs_attr.run([] {
-    return cudaFuncSetAttribute(derivs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes_derivs(kWpb));
+    cudaError_t e = cudaFuncSetAttribute(derivs_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes_derivs(kWpb));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(derivs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes_derivs(kWpb));
+    return e;
   });
 }
 
 // Resident blocks per SM of each persistent pixel kernel, per device (0
 // until measured on that device).
 enum {
-  kOccDerivs, kOccGrad, kOccValue, kOccBackground, kOccRender, kOccCommit, kOccPrepare, kOccKinds
+  kOccDerivs, kOccGrad, kOccValue, kOccDerivsQ, kOccGradQ, kOccValueQ, kOccBackground, kOccRender,
+  kOccCommit, kOccPrepare, kOccKinds
 };
 static std::atomic<int> g_occ[kMaxDevices][kOccKinds] = {};
 static DeviceOnce g_occ_once;
@@ -1257,13 +1312,23 @@ cudaError_t init_pixel_occupancy() {
     const int dev = current_device();
     const size_t sm = smem_bytes(kWpb);
     int occ[kOccKinds] = {};
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccDerivs], derivs_kernel,
-                                                                  kWpb * 32, smem_bytes_derivs(kWpb));
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ[kOccDerivs], derivs_kernel<false>, kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGrad], grad_kernel, kWpb * 32,
-                                                         smem_bytes_grad(kWpb));
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccDerivsQ], derivs_kernel<true>,
+                                                        kWpb * 32, smem_bytes_derivs(kWpb));
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValue], value_kernel, kWpb * 32, sm);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGrad], grad_kernel<false>,
+                                                        kWpb * 32, smem_bytes_grad(kWpb));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccGradQ], grad_kernel<true>,
+                                                        kWpb * 32, smem_bytes_grad(kWpb));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValue], value_kernel<false>,
+                                                        kWpb * 32, sm);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccValueQ], value_kernel<true>,
+                                                        kWpb * 32, sm);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kOccBackground], background_kernel,
                                                         kWpb * 32, sm);
@@ -1303,27 +1368,46 @@ cudaError_t launch_background(const Launch& L, const PlanView& v) {
   return cudaGetLastError();
 }
 
+// The work queue pays when a launch has many items per warp (its claims
+// then balance the warps' finishing times); with few, the grid-stride form
+// (fewer registers, no claims) is faster.
+constexpr int kQueueItemsPerWarp = 8;
+static bool use_queue(const PlanView& v, int blocks) {
+  return v.work_ctr && v.n_items >= kQueueItemsPerWarp * kWpb * blocks;
+}
+
 cudaError_t launch_pixels_derivs(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
   if (cudaError_t e = derivs_attr()) return e;
-  derivs_kernel<<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32, smem_bytes_derivs(kWpb),
-                  L.stream>>>(v, L.n_exp, L.n_dev);
+  const int gq = grid_for(L, v.n_items, kWpb, kOccDerivsQ);
+  if (use_queue(v, gq))
+    derivs_kernel<true><<<gq, kWpb * 32, smem_bytes_derivs(kWpb), L.stream>>>(v, L.n_exp, L.n_dev);
+  else
+    derivs_kernel<false><<<grid_for(L, v.n_items, kWpb, kOccDerivs), kWpb * 32,
+                           smem_bytes_derivs(kWpb), L.stream>>>(v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixels_grad(const Launch& L, const PlanView& v) {
   if (v.n_items == 0) return cudaSuccess;
-  grad_kernel<<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes_grad(kWpb),
-                L.stream>>>(
-      v, L.n_exp, L.n_dev);
+  const int gq = grid_for(L, v.n_items, kWpb, kOccGradQ);
+  if (use_queue(v, gq))
+    grad_kernel<true><<<gq, kWpb * 32, smem_bytes_grad(kWpb), L.stream>>>(v, L.n_exp, L.n_dev);
+  else
+    grad_kernel<false><<<grid_for(L, v.n_items, kWpb, kOccGrad), kWpb * 32, smem_bytes_grad(kWpb),
+                         L.stream>>>(v, L.n_exp, L.n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pixels_value(const Launch& L, const PlanView& v, bool keep_render) {
   if (v.n_items == 0) return cudaSuccess;
   const int mode = !keep_render || !v.cache ? 0 : (v.cache_half ? 2 : 1);
-  value_kernel<<<grid_for(L, v.n_items, kWpb, kOccValue), kWpb * 32, smem_bytes(kWpb), L.stream>>>(
-      v, L.n_exp, L.n_dev, mode);
+  const int gq = grid_for(L, v.n_items, kWpb, kOccValueQ);
+  if (use_queue(v, gq))
+    value_kernel<true><<<gq, kWpb * 32, smem_bytes(kWpb), L.stream>>>(v, L.n_exp, L.n_dev, mode);
+  else
+    value_kernel<false><<<grid_for(L, v.n_items, kWpb, kOccValue), kWpb * 32, smem_bytes(kWpb),
+                          L.stream>>>(v, L.n_exp, L.n_dev, mode);
   return cudaGetLastError();
 }
 
