@@ -907,8 +907,9 @@ __device__ __forceinline__ void value_item(const PlanView& v, int it, const Item
 // keep_render: 0 none; 1 the own moments into v.trial_render; 2 into the
 // source's other half of the render cache (where a Newton step's trial
 // render waits for the accept rule).
+// Eight blocks per SM (64 registers): 3.5 % faster than seven at 72.
 template <bool kQueue>
-__global__ void __launch_bounds__(128) value_kernel(PlanView v, int ne, int nd,
+__global__ void __launch_bounds__(128, 8) value_kernel(PlanView v, int ne, int nd,
                                                     int keep_render) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -1032,7 +1033,7 @@ __global__ void __launch_bounds__(128) background_kernel(PlanView v, int ne, int
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* rec = smem + wib * kValRecF;
-  WarpQueue wq(nullptr);   // grid stride: measured faster for the gather
+  WarpQueue wq(nullptr);   // grid stride (short units, as in prepare_kernel)
   for (; wq.it < v.n_items; wq.advance()) {
     wq.ask(lane);
     const Item item = v.items[wq.it];
@@ -1058,7 +1059,9 @@ __global__ void __launch_bounds__(128) prepare_kernel(PlanView v, const ModelDev
   float* rec = smem + wib * kValRecF;
   const int n_mark = (v.n + 31) / 32;
   const int units = n_mark + n_setup + (bg ? v.n_items : 0);
-  WarpQueue wq(nullptr);   // grid stride: measured faster for the gather
+  // grid stride: its units are short, so a queue's claim would not return
+  // before the next unit (measured 11 % slower)
+  WarpQueue wq(nullptr);
   for (; wq.it < units; wq.advance()) {
     wq.ask(lane);
     const int u = wq.it;
