@@ -178,16 +178,17 @@ struct WarpQueue {
   }
 };
 
-// A lane's pixels q0, q0 + 32, q0 + 64, ... of a row-major patch of width w
-// as (column, row), without a division per pixel: a step of 32 pixels is
-// ay rows and ax columns, plus one row when the column passes w.
+// A lane's pixels q0, q0 + step, q0 + 2 step, ... (step 32 unless given) of
+// a row-major patch of width w as (column, row), without a division per
+// pixel: a step is ay rows and ax columns, plus one row when the column
+// passes w.
 struct PixelWalk {
   int qx, qy, ax, ay;
-  __device__ __forceinline__ PixelWalk(int q0, int w) {
+  __device__ __forceinline__ PixelWalk(int q0, int w, int step = 32) {
     qy = q0 / w;
     qx = q0 - qy * w;
-    ay = 32 / w;
-    ax = 32 - ay * w;
+    ay = step / w;
+    ax = step - ay * w;
   }
   __device__ __forceinline__ void next(int w) {
     qx += ax;
@@ -380,6 +381,52 @@ __device__ __forceinline__ void profiles_value(const float* __restrict__ rec, in
   }
   F0 = fmaf(rec[H_RHO], f.x, rec[H_RHO1] * f.y);
   F1 = fs;
+}
+
+// profiles_value at two pixels (a and b), each with exactly the
+// instructions of profiles_value, reading each staged component once.
+__device__ __forceinline__ void profiles_value2(const float* __restrict__ rec, int ne, int nd,
+                                                float pxa, float pya, float pxb, float pyb,
+                                                float& F0a, float& F1a, float& F0b,
+                                                float& F1b) {
+  const float4* q4 = reinterpret_cast<const float4*>(rec + kCompBase);
+  float fsa = 0.f, fsb = 0.f;
+  float2 fa = make_float2(0.f, 0.f), fb = make_float2(0.f, 0.f);
+  const int per = ne + nd;
+  const int nb = ne < nd ? ne : nd;
+#pragma unroll
+  for (int k = 0; k < kPsf; ++k) {
+    const Offset oa = make_offset(pixel_delta(rec, k, pxa, pya));
+    const Offset ob = make_offset(pixel_delta(rec, k, pxb, pyb));
+    const float4 qs = q4[k];
+    fsa += gauss_density(qs, oa);
+    fsb += gauss_density(qs, ob);
+    const Offset2 a2 = dup_offset(oa), b2 = dup_offset(ob);
+    const float4* g = q4 + kPsf + k * per;
+    for (int j = 0; j < nb; ++j) {
+      const float4 a = g[2 * j], b = g[2 * j + 1];
+      const float2 A11 = make_float2(a.x, a.y), A12 = make_float2(a.z, a.w);
+      const float2 A22 = make_float2(b.x, b.y), lw = make_float2(b.z, b.w);
+      const float2 ga = fma2(A11, a2.xx, fma2(A12, a2.xy, fma2(A22, a2.yy, lw)));
+      const float2 gb = fma2(A11, b2.xx, fma2(A12, b2.xy, fma2(A22, b2.yy, lw)));
+      fa = add2(fa, make_float2(exp2f(ga.x), exp2f(ga.y)));
+      fb = add2(fb, make_float2(exp2f(gb.x), exp2f(gb.y)));
+    }
+    const float4* single = g + 2 * nb;
+    for (int j = nb; j < ne; ++j, ++single) {
+      fa.x += gauss_density(*single, oa);
+      fb.x += gauss_density(*single, ob);
+    }
+    for (int j = nb; j < nd; ++j, ++single) {
+      fa.y += gauss_density(*single, oa);
+      fb.y += gauss_density(*single, ob);
+    }
+  }
+  const float rho = rec[H_RHO], rho1 = rec[H_RHO1];
+  F0a = fmaf(rho, fa.x, rho1 * fa.y);
+  F1a = fsa;
+  F0b = fmaf(rho, fb.x, rho1 * fb.y);
+  F1b = fsb;
 }
 
 // The source's own E_q[l f] and V_q[l f] at a pixel.  V uses the
@@ -882,19 +929,28 @@ __device__ __forceinline__ void value_item(const PlanView& v, int it, const Item
   __syncwarp();
   float rel = 0.f, base = 0.f;
   const int end = item.start + item.count;
-  PixelWalk pw(item.start + lane, pi.w);
-  for (int q = item.start + lane; q < end; q += 32, pw.next(pi.w)) {
-    const int qy = pw.qy, qx = pw.qx;
-    const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
-    const float2 bg = v.bg[pi.bg_base + q];
-    float F0, F1, Es, Vs;
-    profiles_value(rec, ne, nd, (float)qx, (float)qy, F0, F1);
-    own_moments(rec, F0, F1, Es, Vs);
-    if (render) render[q] = make_float2(Es, Vs);
-    const float E = bg.x + Es, V = bg.y + Vs;
-    const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
-    rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
-    base += fmaf(x, __logf(bg.x) - 0.5f * bg.y * rb * rb, -bg.x);
+  // a lane's pixels q and q + 32 in one pass over the staged components; the
+  // sums take pixel q, then q + 32, as one pixel per pass would
+  PixelWalk pa(item.start + lane, pi.w, 64), pb(item.start + lane + 32, pi.w, 64);
+  for (int q = item.start + lane; q < end; q += 64, pa.next(pi.w), pb.next(pi.w)) {
+    const bool has_b = q + 32 < end;
+    float F0[2], F1[2];
+    profiles_value2(rec, ne, nd, (float)pa.qx, (float)pa.qy, (float)pb.qx, (float)pb.qy, F0[0],
+                    F1[0], F0[1], F1[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !has_b) break;
+      const int qq = q + 32 * h, qx = h ? pb.qx : pa.qx, qy = h ? pb.qy : pa.qy;
+      const float x = __ldg(v.pixels + pi.pix_base + (int64_t)qy * pi.stride + qx);
+      const float2 bg = v.bg[pi.bg_base + qq];
+      float Es, Vs;
+      own_moments(rec, F0[h], F1[h], Es, Vs);
+      if (render) render[qq] = make_float2(Es, Vs);
+      const float E = bg.x + Es, V = bg.y + Vs;
+      const float r = __frcp_rn(E), rb = __frcp_rn(bg.x);
+      rel += fmaf(x, log1pf(Es * rb) - 0.5f * V * r * r + 0.5f * bg.y * rb * rb, -Es);
+      base += fmaf(x, __logf(bg.x) - 0.5f * bg.y * rb * rb, -bg.x);
+    }
   }
   rel = warp_sum(rel);
   base = warp_sum(base);
