@@ -59,7 +59,8 @@ static __device__ __forceinline__ void pair_sync() {
 }
 
 struct EpiSmem {
-  double W[kAcc];                  // one pair's sums
+  double Wd[2];                    // one pair's value sums (relative, base)
+  float W[kAcc];                   // one pair's other sums (entries 2..63)
   real th[kNuPad];                 // theta of the source (FP32 copy)
   real gnu[kNuPad];
   real Hnu[kNu * kNu];
@@ -367,6 +368,17 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
 
   double vrel = 0.0, vbase = 0.0;
   if (kMode >= 1) {
+    // the slot's tile sums (its pairs' items are contiguous, 256 B an item)
+    // asked into L2 at once: the pair loop below then reads them from L2,
+    // not from DRAM, pair after pair
+    const int p0 = v.slot_pair_ptr[j], p1 = v.slot_pair_ptr[j + 1];
+    if (p1 > p0) {
+      const int64_t i0 = v.pairs[p0].item_begin, i1 = v.pairs[p1 - 1].item_end;
+      const char* base = reinterpret_cast<const char*>(v.partials + i0 * kAcc);
+      const int64_t lines = (i1 - i0) * (kAcc * (int64_t)sizeof(float) / 128);
+      for (int64_t l = tid; l < lines; l += kEpiThreads)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + 128 * l));
+    }
     for (int e = tid; e < kNuPad; e += kEpiThreads) S.gnu[e] = 0.f;
     for (int e = tid; e < kNuPad; e += kEpiThreads) S.gth[e] = 0.f;
   }
@@ -412,7 +424,7 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
           // the loads are independent of the chain, so they run ahead
           float s0 = 0.f, c0 = 0.f;
           if (kMode == 2 || u < kGradAcc) {
-#pragma unroll 4
+#pragma unroll 8
             for (int it = pi.item_begin; it < pi.item_end; ++it) {
               const float y0 = v.partials[(size_t)it * kAcc + u] - c0;
               const float t0 = s0 + y0;
@@ -420,7 +432,15 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
               s0 = t0;
             }
           }
-          S.W[u] = (double)s0 - (double)c0;
+          // the value sums go on in FP64; the others are used in FP32, and
+          // s0 - c0 rounded once to FP32 equals (float)((double)s0 -
+          // (double)c0): that double difference is exact or off s0 by far
+          // less than half an FP32 unit in the last place
+          if (u < 2) {
+            S.Wd[u] = (double)s0 - (double)c0;
+          } else {
+            S.W[u] = s0 - c0;
+          }
         } else {
           // local affine map, FP32: w_k = sum_a T[k][a] nu_a
           const float cal = (float)im.calib;
@@ -457,7 +477,7 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
         auto hi = [](int a) { return a < 4 ? a + 1 : (a < 6 ? 6 : (a < 9 ? 9 : 10)); };
         if (u < 10) {
           float gl = 0.f;
-          for (int k = lo(u); k < hi(u); ++k) gl += S.T[k * 10 + u] * (float)S.W[2 + k];
+          for (int k = lo(u); k < hi(u); ++k) gl += S.T[k * 10 + u] * S.W[2 + k];
           S.gnu[nu_of(u)] += gl;
         } else if (kMode == 2 && u >= 32 && u < 32 + 55) {
           const int e = u - 32;
@@ -469,7 +489,7 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
             for (int l = lo(c); l < hi(c); ++l) {
               const int kk = k < l ? k : l, ll = k < l ? l : k;
               const bool zero = (kk == 2 || kk == 3) && (ll == 2 || ll == 3);
-              const float hwv = zero ? 0.f : (float)S.W[hidx(kk, ll)];
+              const float hwv = zero ? 0.f : S.W[hidx(kk, ll)];
               val = fmaf(S.T[k * 10 + a] * S.T[l * 10 + c], hwv, val);
             }
           const int na = nu_of(a), nc = nu_of(c);
@@ -477,8 +497,8 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
           if (na != nc) S.Hnu[nc * kNu + na] += val;
         }
         if (u == 0) {
-          vr += S.W[0];
-          vb += S.W[1];
+          vr += S.Wd[0];
+          vb += S.Wd[1];
         }
         pair_sync();
       }
