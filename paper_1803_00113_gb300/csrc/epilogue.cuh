@@ -51,6 +51,7 @@ static __device__ __forceinline__ real softplus(real t) {
 
 constexpr int kEpiThreads = 128;   // four warps per source
 constexpr int kPairThreads = kEpiThreads - 32;   // warps 1..3: the pixel sums
+constexpr int kPairGroup = 4;                    // pairs reduced together
 
 // Barrier among the kPairThreads threads of warps 1..3 (named barrier 1;
 // warp 0 is busy with the KL terms meanwhile).
@@ -59,8 +60,8 @@ static __device__ __forceinline__ void pair_sync() {
 }
 
 struct EpiSmem {
-  double Wd[2];                    // one pair's value sums (relative, base)
-  float W[kAcc];                   // one pair's other sums (entries 2..63)
+  double Wd[kPairGroup][2];        // per pair of a group: value sums (relative, base)
+  float W[kPairGroup][kAcc];       // per pair of a group: the other sums (entries 2..63)
   real th[kNuPad];                 // theta of the source (FP32 copy)
   real gnu[kNuPad];
   real Hnu[kNu * kNu];
@@ -74,7 +75,7 @@ struct EpiSmem {
   real klc[2 * kMaxColor * kKlVals];   // colour-bound pieces per (type, component)
   real klj[2 * kMaxColor];         // log w_j - K_j
   real kls[8];                     // scalar KL pieces
-  float T[10 * 10];                // per-image affine map w <- nu (local)
+  float T[kPairGroup][10 * 10];    // per pair of a group: affine map w <- nu (local)
   double red[2][kEpiThreads / 32]; // per-warp value sums
   double vsum[2];                  // the source's value sums (relative, base)
 };
@@ -415,90 +416,127 @@ static __device__ __forceinline__ void epilogue_source(const PlanView& v,
         vb = S.red[1][0] + S.red[1][1] + S.red[1][2];
       }
     } else {
-      for (int pp = v.slot_pair_ptr[j]; pp < v.slot_pair_ptr[j + 1]; ++pp) {
-        const PairInfo pi = v.pairs[pp];
-        const celeste_image& im = v.images[pi.image];
+      // kPairGroup pairs at a time: their tile sums in one loop (loads of
+      // every pair in flight together) and their images' maps, then the
+      // per-pair updates in pair order; each sum below is updated by one
+      // thread, pair after pair, as with one pair at a time
+      const int pend = v.slot_pair_ptr[j + 1];
+      for (int pp = v.slot_pair_ptr[j]; pp < pend; pp += kPairGroup) {
+        const int ng = min(kPairGroup, pend - pp);
         if (u < kAcc) {
-          // the pair's tile sums, accumulator u: compensated (Kahan) FP32
+          // the pairs' tile sums, accumulator u: compensated (Kahan) FP32
           // summation whose error does not grow with the number of tiles;
-          // the loads are independent of the chain, so they run ahead
-          float s0 = 0.f, c0 = 0.f;
-          if (kMode == 2 || u < kGradAcc) {
-#pragma unroll 8
-            for (int it = pi.item_begin; it < pi.item_end; ++it) {
-              const float y0 = v.partials[(size_t)it * kAcc + u] - c0;
-              const float t0 = s0 + y0;
-              c0 = (t0 - s0) - y0;
-              s0 = t0;
+          // the loads are independent of the chains, so they run ahead
+          float s0[kPairGroup], c0[kPairGroup];
+          int ib[kPairGroup], nit[kPairGroup];
+          int nmax = 0;
+#pragma unroll
+          for (int g = 0; g < kPairGroup; ++g) {
+            s0[g] = c0[g] = 0.f;
+            ib[g] = nit[g] = 0;
+            if (g < ng && (kMode == 2 || u < kGradAcc)) {
+              ib[g] = v.pairs[pp + g].item_begin;
+              nit[g] = v.pairs[pp + g].item_end - ib[g];
+              nmax = max(nmax, nit[g]);
+            }
+          }
+#pragma unroll 4
+          for (int t = 0; t < nmax; ++t) {
+#pragma unroll
+            for (int g = 0; g < kPairGroup; ++g) {
+              if (t < nit[g]) {
+                const float y0 = v.partials[(size_t)(ib[g] + t) * kAcc + u] - c0[g];
+                const float t0 = s0[g] + y0;
+                c0[g] = (t0 - s0[g]) - y0;
+                s0[g] = t0;
+              }
             }
           }
           // the value sums go on in FP64; the others are used in FP32, and
           // s0 - c0 rounded once to FP32 equals (float)((double)s0 -
           // (double)c0): that double difference is exact or off s0 by far
           // less than half an FP32 unit in the last place
-          if (u < 2) {
-            S.Wd[u] = (double)s0 - (double)c0;
-          } else {
-            S.W[u] = s0 - c0;
+#pragma unroll
+          for (int g = 0; g < kPairGroup; ++g) {
+            if (g < ng) {
+              if (u < 2) {
+                S.Wd[g][u] = (double)s0[g] - (double)c0[g];
+              } else {
+                S.W[g][u] = s0[g] - c0[g];
+              }
+            }
           }
         } else {
-          // local affine map, FP32: w_k = sum_a T[k][a] nu_a
-          const float cal = (float)im.calib;
-          const float A0 = (float)im.wcs_A[0], A1 = (float)im.wcs_A[1];
-          const float A2 = (float)im.wcs_A[2], A3 = (float)im.wcs_A[3];
-          for (int e = u - kAcc; e < 100; e += kPairThreads - kAcc) {
-            float t = 0.f;
-            switch (e) {
-              case 0: case 11: t = cal; break;
-              case 22: case 33: t = cal * cal; break;
-              case 44: t = A0; break;
-              case 45: t = A1; break;
-              case 54: t = A2; break;
-              case 55: t = A3; break;
-              case 66: t = A0 * A0; break;
-              case 67: t = 2.f * A0 * A1; break;
-              case 68: t = A1 * A1; break;
-              case 76: t = A0 * A2; break;
-              case 77: t = A0 * A3 + A1 * A2; break;
-              case 78: t = A1 * A3; break;
-              case 86: t = A2 * A2; break;
-              case 87: t = 2.f * A2 * A3; break;
-              case 88: t = A3 * A3; break;
-              case 99: t = 1.f; break;
-              default: break;
+          // each pair's local affine map, FP32: w_k = sum_a T[k][a] nu_a
+          for (int g = 0; g < ng; ++g) {
+            const celeste_image& im = v.images[v.pairs[pp + g].image];
+            const float cal = (float)im.calib;
+            const float A0 = (float)im.wcs_A[0], A1 = (float)im.wcs_A[1];
+            const float A2 = (float)im.wcs_A[2], A3 = (float)im.wcs_A[3];
+            for (int e = u - kAcc; e < 100; e += kPairThreads - kAcc) {
+              float t = 0.f;
+              switch (e) {
+                case 0: case 11: t = cal; break;
+                case 22: case 33: t = cal * cal; break;
+                case 44: t = A0; break;
+                case 45: t = A1; break;
+                case 54: t = A2; break;
+                case 55: t = A3; break;
+                case 66: t = A0 * A0; break;
+                case 67: t = 2.f * A0 * A1; break;
+                case 68: t = A1 * A1; break;
+                case 76: t = A0 * A2; break;
+                case 77: t = A0 * A3 + A1 * A2; break;
+                case 78: t = A1 * A3; break;
+                case 86: t = A2 * A2; break;
+                case 87: t = 2.f * A2 * A3; break;
+                case 88: t = A3 * A3; break;
+                case 99: t = 1.f; break;
+                default: break;
+              }
+              S.T[g][e] = t;
             }
-            S.T[e] = t;
           }
         }
         pair_sync();
-        const int b = im.band;
-        auto nu_of = [b](int a) { return a < 4 ? 4 * b + a : 16 + a; };   // 4..9 -> 20..25
         auto lo = [](int a) { return a < 4 ? a : (a < 6 ? 4 : (a < 9 ? 6 : 9)); };
         auto hi = [](int a) { return a < 4 ? a + 1 : (a < 6 ? 6 : (a < 9 ? 9 : 10)); };
         if (u < 10) {
-          float gl = 0.f;
-          for (int k = lo(u); k < hi(u); ++k) gl += S.T[k * 10 + u] * S.W[2 + k];
-          S.gnu[nu_of(u)] += gl;
+          for (int g = 0; g < ng; ++g) {
+            const int b = v.pairs[pp + g].band;
+            const float* T = S.T[g];
+            const float* W = S.W[g];
+            float gl = 0.f;
+            for (int k = lo(u); k < hi(u); ++k) gl += T[k * 10 + u] * W[2 + k];
+            S.gnu[u < 4 ? 4 * b + u : 16 + u] += gl;    // nu of w_u (4..9 -> 20..25)
+          }
         } else if (kMode == 2 && u >= 32 && u < 32 + 55) {
           const int e = u - 32;
           int a = 0, rem = e;
           while (rem >= 10 - a) { rem -= 10 - a; ++a; }
           const int c = a + rem;
-          float val = 0.f;
-          for (int k = lo(a); k < hi(a); ++k)
-            for (int l = lo(c); l < hi(c); ++l) {
-              const int kk = k < l ? k : l, ll = k < l ? l : k;
-              const bool zero = (kk == 2 || kk == 3) && (ll == 2 || ll == 3);
-              const float hwv = zero ? 0.f : S.W[hidx(kk, ll)];
-              val = fmaf(S.T[k * 10 + a] * S.T[l * 10 + c], hwv, val);
-            }
-          const int na = nu_of(a), nc = nu_of(c);
-          S.Hnu[na * kNu + nc] += val;
-          if (na != nc) S.Hnu[nc * kNu + na] += val;
+          for (int g = 0; g < ng; ++g) {
+            const int b = v.pairs[pp + g].band;
+            const float* T = S.T[g];
+            const float* W = S.W[g];
+            float val = 0.f;
+            for (int k = lo(a); k < hi(a); ++k)
+              for (int l = lo(c); l < hi(c); ++l) {
+                const int kk = k < l ? k : l, ll = k < l ? l : k;
+                const bool zero = (kk == 2 || kk == 3) && (ll == 2 || ll == 3);
+                const float hwv = zero ? 0.f : W[hidx(kk, ll)];
+                val = fmaf(T[k * 10 + a] * T[l * 10 + c], hwv, val);
+              }
+            const int na = a < 4 ? 4 * b + a : 16 + a, nc = c < 4 ? 4 * b + c : 16 + c;
+            S.Hnu[na * kNu + nc] += val;
+            if (na != nc) S.Hnu[nc * kNu + na] += val;
+          }
         }
         if (u == 0) {
-          vr += S.Wd[0];
-          vb += S.Wd[1];
+          for (int g = 0; g < ng; ++g) {
+            vr += S.Wd[g][0];
+            vb += S.Wd[g][1];
+          }
         }
         pair_sync();
       }
