@@ -7,7 +7,7 @@ accumulation on the device):
     scale sum_pix |term - term_absent| + |KL|;
   * gradient and Hessian entries: |d| <= 1e-4 max(|ref|, scale), the scale
     being the sum over pixels of the absolute per-pixel derivative (plus the
-    KL's), so entries that cancel to ~0 over the patch are judged against
+    KL's), so entries that cancel to ~0 over the patch are compared with
     the magnitudes that were summed.
 """
 import math
