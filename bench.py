@@ -751,7 +751,7 @@ def run_reference(args):
     problem, cfg = workload(args.workload, args.sources, SEED + 1)
     rng = np.random.default_rng(0)
     order = list(rng.permutation(problem.n_sources))
-    per_step = 2
+    per_step = 1
     times, visits = [], 0
     k = 0
     for i in range(args.warmup + args.steps):
