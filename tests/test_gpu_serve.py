@@ -61,10 +61,10 @@ def test_a_request_arriving_mid_run_joins_at_a_pass_boundary(cel):
     import time
     big = fields.region_request(777, n_sources=64, side=400)
     small = fields.region_request(702, n_sources=2, side=40)
-    srv = cel.Server(small.model, workers=1)
-    alone = _collect(srv, [srv.submit(small)]).popitem()[1]
-    srv.close()
     srv = cel.Server(big.model, workers=1)
+    # the small request alone first: it also leaves the worker set up and
+    # idle, so the big request is admitted as soon as it is submitted
+    alone = _collect(srv, [srv.submit(small)]).popitem()[1]
     t_big = srv.submit(big)
     time.sleep(0.02)                       # the big request is on the GPU
     t_small = srv.submit(small)
